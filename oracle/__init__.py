@@ -1,0 +1,13 @@
+"""FP64 CPU oracle for the graded-material BEM hot path.
+
+TEST INFRASTRUCTURE ONLY.  Only tests/, ``__graft_entry__.smoke()`` and the CPU
+baseline / reference leg of ``bench.py`` may import, call, link or run anything
+under oracle/.  The product library (paper_1612_08395_gb300) never touches it,
+and it never imports the product: the two share no code.
+
+Parity status: every function is pinned by the tests in tests/test_oracle_*.py
+except alpha(k, nu) for k != 0, which is "parity unpinned": every closed form
+the paper offers carries the same alpha, so an error in Eq. 3 would cancel.
+"""
+from .bem_oracle import *  # noqa: F401,F403
+from . import closed_forms  # noqa: F401

@@ -1,0 +1,105 @@
+"""Planted mistakes in the oracle, each caught by a pin.
+
+Each test rewrites one line of an oracle function (in memory, on the CPU),
+then runs a pin from test_oracle_pins.py's families against the mutant and
+checks that the pin now fails.  This shows the pins would catch that kind of
+error in the real oracle.  The oracle files on disk are never modified.
+"""
+import inspect
+import textwrap
+
+import numpy as np
+import pytest
+
+from paper_1612_08395_gb300 import inputs as I
+
+
+def _mutant(func, old, new):
+    src = textwrap.dedent(inspect.getsource(func))
+    assert old in src, f"mutation anchor not found: {old!r}"
+    ns = dict(func.__globals__)
+    exec(compile(src.replace(old, new, 1), f"<mutant {func.__name__}>", "exec"), ns)
+    return ns[func.__name__]
+
+
+def _hertz_force_rel_error(oracle_mod, compliance):
+    from oracle import closed_forms as CF
+    n, k, nu, d = 32, 0.5, 0.3, 0.01
+    dx = 1.0 / n
+    A = compliance(k, nu)
+    conv = oracle_mod.FFTConvolver(oracle_mod.influence_quarter(k, dx, dx, n + 1, n + 1), n, n)
+    res = oracle_mod.pk_solve(A, conv, I.paraboloid(n), d)
+    F = dx * dx * res.p.sum()
+    return abs(F / CF.hertz_force(CF.hertz_radius(d, k, 1.0), k, nu, 1.0) - 1)
+
+
+def test_dropped_poisson_factor_is_caught(oracle_mod):
+    assert _hertz_force_rel_error(oracle_mod, oracle_mod.compliance) < 0.02
+    bad = _mutant(oracle_mod.compliance, "(1.0 - nu * nu)", "1.0")
+    assert _hertz_force_rel_error(oracle_mod, bad) > 0.05
+
+
+def test_transposed_kernel_is_caught(oracle_mod):
+    # Non-square cells (dy = 2 dx): building the torus from the transposed table
+    # breaks FFT-equals-direct.
+    n = 12
+    Kq = oracle_mod.influence_quarter(-0.4, 1.0 / n, 2.0 / n, n + 1, n + 1)
+    p = I.random_pressure(n, n, seed=4)
+    ud = oracle_mod.convolve_direct(Kq[:n, :n], p)
+    bad_torus = _mutant(oracle_mod.torus_kernel, "Kq[np.ix_(iy, ix)]", "Kq.T[np.ix_(iy, ix)]")
+
+    def fft_conv(torus):
+        return np.fft.irfft2(np.fft.rfft2(np.pad(p, ((0, n), (0, n))))
+                             * np.fft.rfft2(torus(Kq, 2 * n, 2 * n)), s=(2 * n, 2 * n))[:n, :n]
+
+    assert np.abs(fft_conv(oracle_mod.torus_kernel) - ud).max() < 1e-12 * np.abs(ud).max()
+    assert np.abs(fft_conv(bad_torus) - ud).max() > 1e-3 * np.abs(ud).max()
+
+
+def test_overlap_sign_is_caught(oracle_mod):
+    import itertools
+    n, k, nu = 3, 0.3, 0.3
+    dx = 1.0 / n
+    A = oracle_mod.compliance(k, nu)
+    Kq = oracle_mod.influence_quarter(k, dx, dx, n + 1, n + 1)
+    rng = np.random.Generator(np.random.PCG64(1))
+    h = rng.random((n, n)) * 0.01
+    d = 0.006
+    Kfull = np.array([[Kq[abs(a // n - b // n), abs(a % n - b % n)] for b in range(n * n)]
+                      for a in range(n * n)])
+    ref = None
+    for mask in itertools.product([False, True], repeat=n * n):
+        S = np.array(mask)
+        p = np.zeros(n * n)
+        if S.any():
+            p[S] = np.linalg.solve(A * Kfull[np.ix_(S, S)], (d - h.ravel())[S])
+        g = A * Kfull @ p + h.ravel() - d
+        if (p >= -1e-14).all() and (g[~S] >= -1e-14).all():
+            ref = p
+    bad = _mutant(oracle_mod.pk_solve, "p = np.where(Iol, -tau * g, p)",
+                  "p = np.where(Iol, tau * g, p)")
+    conv = oracle_mod.DirectConvolver(Kq, n, n)
+    # start from one loaded element so that the overlap step has to bring in the rest
+    p0 = np.zeros((n, n))
+    p0[1, 1] = 1e-3
+    good = oracle_mod.pk_solve(A, conv, h, d, p0=p0, tol=1e-14).p.ravel()
+    assert np.allclose(good, ref, rtol=1e-9, atol=1e-12)
+    res = bad(A, conv, h, d, p0=p0, tol=1e-14, max_iter=300)
+    assert not np.allclose(res.p.ravel(), ref, rtol=1e-6, atol=1e-9)
+
+
+def test_detach_sign_is_caught(oracle_mod):
+    from oracle import closed_forms as CF
+    n, k, nu, a, gam = 32, 0.0, 0.3, 0.2, 1e-3
+    dx = 1.0 / n
+    A = oracle_mod.compliance(k, nu)
+    conv = oracle_mod.FFTConvolver(oracle_mod.influence_quarter(k, dx, dx, n + 1, n + 1), n, n)
+    dc = CF.flat_punch_dcrit(a, k, nu, gam)
+    steps = np.linspace(0.0, -1.3 * dc, 66)[1:]
+    pc = oracle_mod.p_crit(k, nu, gam, dx)
+    bad = _mutant(oracle_mod.adhesive_unload, "D = S & (-p > pcrit)", "D = S & (p > pcrit)")
+    for fn, ok in ((oracle_mod.adhesive_unload, True), (bad, False)):
+        out, _, _ = fn(A, conv, I.flat_punch(n, a), 0.2 * dc, steps, pc, dx * dx)
+        lost = [o["d"] for o in out if o["count"] == 0]
+        caught = bool(lost) and abs(lost[0] / -dc - 1) < 0.1
+        assert caught == ok
