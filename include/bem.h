@@ -1,0 +1,169 @@
+/*
+ * bem.h -- C ABI of the GB300 (sm_103a) boundary element solver for normal
+ * non-adhesive and adhesive contact of a power-law graded elastic half-space,
+ * E(z) = E0 (z/c0)^k with -1 < k < 1 (Li & Popov, arXiv 1612.08395).
+ *
+ * Conventions shared by every entry point
+ *   - Grid: Nx x Ny square-or-rectangular elements of sides dx, dy; fields are
+ *     row-major arrays of Ny rows of Nx doubles, element (iy, ix) at iy*Nx+ix.
+ *     Element centres are x_i = (i - Nx/2 + 1/2) dx (domain centre on a node).
+ *   - Sign: pressure p > 0 is compressive; the gap is g = A (K*p) + h - d with
+ *     A = alpha(k,nu) (1-nu^2) c0^k / E0 (Eqs. 2, 7, 12) and h >= 0 the height
+ *     of the indenter above its lowest point, d the indentation depth.
+ *   - Pointers: every array argument may be a host pointer or a CUDA device
+ *     pointer on the handle's device; the library tells them apart with
+ *     cudaPointerGetAttributes.  The caller owns all buffers passed in; the
+ *     handle owns its own device memory and stream.
+ *   - Errors: functions return BEM_OK (0) or a negative BEM_E* code and set a
+ *     thread-local message readable with bem_last_error().  No entry point
+ *     aborts the process or traps the GPU; device-side waits are bounded.
+ *   - Threads: one handle must not be used by two host threads at once.
+ *     Distinct handles are independent.
+ */
+#ifndef BEM_GB300_H
+#define BEM_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BEM_OK 0
+#define BEM_EINVAL (-1)   /* bad argument: k, nu, sizes, depths, pointers      */
+#define BEM_ENOMEM (-2)   /* device or pinned allocation failed                 */
+#define BEM_ENOCONV (-3)  /* CG hit max_iter; results are the last iterate      */
+#define BEM_ENUMERIC (-4) /* NaN/Inf met in a reduction                         */
+#define BEM_ETIMEOUT (-5) /* a bounded device-side wait gave up                 */
+#define BEM_ECUDA (-6)    /* a CUDA runtime call failed                         */
+
+/* Arithmetic of the transform and the fields.  BEM_PREC_FP64: everything in
+ * FP64 (the plain path).  BEM_PREC_FP32: FFT passes and fields in FP32, CG
+ * scalars and all reductions in FP64.  BEM_PREC_FP32_REFINE: FP32 solve, then
+ * FP64-residual refinement sweeps on the final contact set. */
+#define BEM_PREC_FP64 0
+#define BEM_PREC_FP32 1
+#define BEM_PREC_FP32_REFINE 2
+
+/* Record CUDA events around the three transform passes of the first CG
+ * iteration of every captured chunk (read back with bem_pass_times). */
+#define BEM_FLAG_TIME_PASSES 1
+
+typedef struct bem_ctx *bem_handle;
+
+typedef struct {
+  double tol;         /* stopping tolerance; 0 = default 1e-10 (FP64) / 1e-6 (FP32) */
+  int max_iter;       /* CG iteration cap per solve; 0 = default 20000               */
+  int precision;      /* BEM_PREC_*                                                  */
+  int refine_sweeps;  /* FP32_REFINE: max refinement sweeps; 0 = default 3           */
+  int flags;          /* BEM_FLAG_* bits, 0 = none                                   */
+  void *stream;       /* cudaStream_t to order work after; NULL = handle's own      */
+} bem_opts;
+
+typedef struct {
+  double force;             /* F = dx dy sum p  (Sec. 3.1: "sum of pressures")    */
+  double area;              /* dx dy * number of elements in contact              */
+  double contact_radius;    /* sqrt(area / pi)                                     */
+  double final_eps;         /* last CG stopping measure                            */
+  double max_gap_violation; /* max over contact of |g|, and of -g off contact      */
+  double depth;             /* d of this solve                                     */
+  int iterations;           /* CG iterations (all rounds of this step)             */
+  int detach_rounds;        /* adhesive: detach-and-resolve rounds                 */
+  int contact_count;        /* elements in contact                                 */
+  int status;               /* BEM_OK or BEM_ENOCONV / BEM_ENUMERIC                */
+} bem_result;
+
+/* ---------------------------------------------------------------------------
+ * bem_create: validate, compute A (Eqs. 2-4, 12), tabulate the influence
+ * coefficients K(di, dj) of Eq. 9 for 0 <= di <= Px/2, 0 <= dj <= Py/2 in FP64
+ * on the device, wrap them evenly onto the Px x Py torus (Px, Py = powers of two
+ * >= 2 Nx, 2 Ny, at least 16), and take its spectrum (Eq. 13: FFT(K)), kept as
+ * the real quarter in FP64 and FP32.
+ *   Nx, Ny : 2..4096;  dx, dy > 0;  -1 < k < 1;  -1 < nu <= 0.5 with
+ *   beta(k,nu)^2 > 0 (Eq. 4);  E0 > 0;  c0 > 0;  out != NULL.
+ * The handle creates its own non-blocking stream on the current device.
+ * Returns BEM_EINVAL, BEM_ENOMEM or BEM_ECUDA on failure (*out untouched). */
+int bem_create(int Nx, int Ny, double dx, double dy, double k, double nu, double E0, double c0,
+               bem_handle *out);
+
+void bem_destroy(bem_handle h);
+
+/* Thread-local text of the last error ("" if none). */
+const char *bem_last_error(void);
+
+/* ---------------------------------------------------------------------------
+ * Non-adhesive (dgamma <= 0): solve the contact problem p >= 0, g >= 0,
+ * p g = 0 at depth d by the constrained conjugate-gradient method (Sec. 2.1,
+ * Polonsky & Keer), each iteration applying u = A K*p as the zero-padded FFT
+ * convolution of Eq. 13.
+ * Adhesive (dgamma > 0, Sec. 3.1): preload non-adhesively to d_preload (>= d),
+ * then hold the contact area, solve for p at depth d, detach every element with
+ * tensile stress -p > p_crit (Eq. 24, corrected c1 of Table 1), and repeat
+ * until none detaches.  Requires dx == dy (Eq. 24 is for square elements).
+ *   profile      : Nx*Ny heights h >= 0 (host or device)
+ *   opts         : NULL for defaults
+ *   pressure_out : Nx*Ny FP64 pressures, may be NULL
+ *   res          : must not be NULL
+ * Returns BEM_OK, BEM_ENOCONV (res filled), BEM_ENUMERIC, BEM_EINVAL, BEM_ECUDA. */
+int bem_solve(bem_handle h, const double *profile, double d, double dgamma, double d_preload,
+              const bem_opts *opts, double *pressure_out, bem_result *res);
+
+/* ---------------------------------------------------------------------------
+ * Load-unload sweep over nsteps depths (Figs. 3b, 6, 7): each step starts from
+ * the previous step's pressures.  dgamma <= 0: every step is a non-adhesive
+ * solve.  dgamma > 0: step 0 is the non-adhesive preload at d_steps[0] and steps
+ * 1.. are adhesive pull-off steps (Sec. 3.1 algorithm); d_steps must then be
+ * non-increasing and dx == dy.  per_step[nsteps] receives one result per step;
+ * final_pressure (Nx*Ny, may be NULL) the last step's pressures.
+ * Returns the first non-OK status met (remaining steps still run unless the
+ * error is BEM_EINVAL / BEM_ECUDA / BEM_ENUMERIC). */
+int bem_sweep(bem_handle h, const double *profile, const double *d_steps, int nsteps,
+              double dgamma, const bem_opts *opts, bem_result *per_step, double *final_pressure);
+
+/* ---------------------------------------------------------------------------
+ * Building blocks, exposed for verification.
+ *
+ * bem_influence_table: copy the FP64 influence coefficients K(di, dj) of Eq. 9
+ *   (integral of (a^2+b^2)^-(1+k)/2 over the element at offset (di, dj)) into
+ *   out[dj*(Px/2+1) + di], 0 <= di <= Px/2, 0 <= dj <= Py/2.
+ * bem_spectrum: copy the FP64 real quarter of FFT(K) on the Px x Py torus into
+ *   out[ky*(Px/2+1) + kx], 0 <= kx <= Px/2, 0 <= ky <= Py/2 (unnormalised).
+ * bem_convolve: u = A K*p (Eq. 7 via Eq. 13) for one Nx*Ny field, in the given
+ *   precision (BEM_PREC_FP64 or BEM_PREC_FP32); p and u are FP64 arrays. */
+int bem_influence_table(bem_handle h, double *out);
+int bem_spectrum(bem_handle h, double *out);
+int bem_convolve(bem_handle h, int precision, const double *p, double *u);
+
+typedef struct {
+  int Nx, Ny, Px, Py;
+  double dx, dy, k, nu, E0, c0;
+  double alpha;      /* Eq. 3                                        */
+  double compliance; /* A = alpha (1-nu^2) c0^k / E0 (Eq. 12)         */
+  size_t device_bytes; /* device memory held by the handle            */
+  unsigned long long kernel_launches; /* kernels launched by this handle so far */
+} bem_info;
+
+int bem_get_info(bem_handle h, bem_info *info);
+
+/* Accumulated device time of the transform passes recorded under
+ * BEM_FLAG_TIME_PASSES: ms[0..2] = total milliseconds of passes A (row FFT and
+ * CG prologue), B (column FFT, spectrum multiply, inverse column FFT) and C
+ * (inverse row FFT and CG epilogue), count[0] = number of timed iterations,
+ * count[1] = of those, iterations of the fixed-set loop.  reset != 0 clears the
+ * totals after reading.  Events are timed on the handle's stream, the stream
+ * the passes run on. */
+int bem_pass_times(bem_handle h, double ms[3], long long count[2], int reset);
+
+/* ---------------------------------------------------------------------------
+ * Host-only helpers (no GPU needed).
+ * bem_alpha: alpha(k, nu) of Eq. 3 (NaN outside the valid range).
+ * bem_c1_corrected: corrected c1(k) of Table 1 for -0.9 <= k <= 0.9; between
+ *   grid points a natural cubic spline of ln c1 (NaN outside).
+ * bem_p_crit: critical tensile stress of Eq. 24 for square elements of side
+ *   delta, work of adhesion dgamma (NaN on invalid input). */
+double bem_alpha(double k, double nu);
+double bem_c1_corrected(double k);
+double bem_p_crit(double k, double nu, double E0, double c0, double dgamma, double delta);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BEM_GB300_H */

@@ -1,0 +1,115 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace bem {
+
+// Launch geometry of the three convolution passes for one handle.
+//   rows  : field rows (Ny), cols: field columns (Nx)
+//   Px,Py : torus sides (powers of two >= 2 Nx, 2 Ny, >= 16); M = Px/2
+//   W     : intermediate spectrum, (M+1) rows (kx = 0..M) of `rows` complex
+//           values: row kx holds column kx of the row transforms (transposed
+//           so the column pass reads contiguous memory).
+struct Plan {
+  int nx, ny, px, py, M, logM, logPy;
+  int nbA;    // field rows per CTA in passes A and C
+  int nbB;    // spectrum columns per CTA in pass B
+  int gridA;  // = ceil(ny / nbA)
+  int gridB;  // = ceil(M / nbB)   (column 0 CTA also carries column M)
+  int threadsA, threadsB;
+  size_t smemA, smemB, smemC;
+};
+
+// Device-resident scalar state of one CG solve (FP64 throughout).
+struct Scalars {
+  double tol;        // stopping tolerance
+  double tau, beta, delta, G, G_old, eps, bnorm, pcrit;
+  double sum_p, sum_dp, n_ol, n_ic, str;
+  int max_iter, iter, done, status, have_tau, pad0;
+  unsigned int cnt_a, cnt_c, cnt_e, cnt_r;  // last-block arrival counters
+};
+
+enum { SC_OK = 0, SC_NOCONV = 1, SC_NUMERIC = 2 };
+
+// Pass A (row real-to-complex FFT) prologue modes.
+enum PassAMode {
+  A_PLAIN = 0,  // x = src
+  A_PK_P = 1,   // Polonsky-Keer update of p (steps 7-8), partials sum|dp|, sum p, #overlap
+  A_PK_T = 2,   // t = (p > 0) ? g + beta t : 0
+  A_CG_T = 3,   // t = S ? g + beta t : 0
+  A_TORUS = 4   // x = K on the even torus (spectrum set-up, FP64)
+};
+// Pass C (row complex-to-real FFT) epilogue modes.
+enum PassCMode {
+  C_PLAIN = 0,  // dst = u
+  C_PK_G = 1,   // g = u + c; partial sum_{p>0} g^2, #(p>0); last block: eps, delta, beta
+  C_PK_R = 2,   // partials sum_{p>0} g t, sum_{p>0} r t; last block: tau
+  C_CG_R = 3,   // r = S ? u : 0 (stored); partial sum t r; last block: tau
+  C_CG_G = 4,   // g = S ? u + c : 0; partials sum g^2, sum_S c^2; last block: G, bnorm
+  C_GAP = 5     // g = u + c (no mask) -- FP64 residual of the refinement
+};
+enum PassBMode { B_CONV = 0, B_SPECTRUM = 1 };
+
+template <typename T>
+struct Fields {
+  T* p;        // pressure
+  T* g;        // gap / residual
+  T* t;        // CG direction
+  T* r;        // A K t
+  T* c;        // offset h - d (or a residual offset)
+  uint8_t* S;  // fixed contact set (adhesive / refinement)
+  const T* src;  // A_PLAIN source
+  T* dst;        // C_PLAIN destination
+};
+
+template <typename T>
+struct PassArgs {
+  Plan pl;
+  Fields<T> f;
+  void* W;              // C<T>[(M+1) * rows_w]
+  int rows_w;           // row length of W (= ny, or Py for the spectrum)
+  int nrows_in;         // rows fed to pass A (= ny, or Py for the torus)
+  int ncols_in;         // columns fed to pass A (= nx, or Px for the torus)
+  const double* kq64;   // A_TORUS: influence quarter, (Py/2+1) x (M+1)
+  const T* khat;        // B_CONV: spectrum quarter, transposed: [kx][ky], ky <= Py/2
+  double* khat64_out;   // B_SPECTRUM outputs ([kx][ky])
+  float* khat32_out;
+  double uscale;        // pass C: A / (Px Py)
+  double* partA;        // per-CTA partials, 4 per CTA
+  double* partC;
+  Scalars* sc;
+};
+
+template <typename T> void launch_pass_a(const PassArgs<T>& a, int mode, cudaStream_t s);
+template <typename T> void launch_pass_b(const PassArgs<T>& a, int mode, cudaStream_t s);
+template <typename T> void launch_pass_c(const PassArgs<T>& a, int mode, cudaStream_t s);
+
+// Elementwise kernels.
+template <typename T> void launch_pk_init(const Plan& pl, const double* h64, double d, T* c, T* p,
+                                          T* t, int warm, int ngrid, cudaStream_t s);
+template <typename T> void launch_cg_update(const Plan& pl, Fields<T> f, double* part, Scalars* sc,
+                                            int ngrid, cudaStream_t s);
+template <typename T> void launch_detach(const Plan& pl, Fields<T> f, double* part, Scalars* sc,
+                                         int ngrid, cudaStream_t s);
+template <typename T> void launch_stats(const Plan& pl, const T* p, const T* g, const uint8_t* S,
+                                        int use_set, double* part, double* out, int ngrid,
+                                        cudaStream_t s);
+template <typename T> void launch_convert_in(const double* src, T* dst, size_t n, cudaStream_t s);
+template <typename T> void launch_convert_out(const T* src, double* dst, size_t n, cudaStream_t s);
+template <typename T> void launch_offset(const double* h64, double d, T* c, size_t n, cudaStream_t s);
+template <typename T> void launch_set_from_p(const T* p, uint8_t* S, size_t n, cudaStream_t s);
+template <typename T> void launch_mask_field(T* x, const uint8_t* S, size_t n, cudaStream_t s);
+void launch_refine_apply(double* p64, const float* dp, const uint8_t* S, int project, size_t n,
+                         cudaStream_t s);
+void launch_to_f32(const double* src, float* dst, size_t n, cudaStream_t s);
+// S = (p > 0) or (g < 0): active set of the refinement sweep.
+void launch_active_set(const double* p, const double* g, uint8_t* S, size_t n, cudaStream_t s);
+
+// Influence coefficients (FP64): Kq[dj*(hx) + di], 0 <= di < hx, 0 <= dj < hy.
+int influence_init_nodes();
+void launch_influence(double* Kq, int hx, int hy, double dx, double dy, double k, cudaStream_t s);
+
+
+}  // namespace bem

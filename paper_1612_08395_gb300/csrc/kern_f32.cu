@@ -1,0 +1,7 @@
+// FP32 instantiation of the convolution passes and elementwise kernels.
+#include "conv_kernels.cuh"
+
+namespace bem {
+BEM_INSTANTIATE(float)
+template void set_smem_attrs<float>();
+}  // namespace bem

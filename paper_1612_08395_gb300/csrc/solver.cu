@@ -1,0 +1,818 @@
+// Host orchestration of the solver: handle set-up (influence table and
+// spectrum), the constrained and fixed-set conjugate-gradient loops as chunks
+// of captured CUDA graphs, the adhesive detach loop, the FP64 refinement
+// sweep, load-unload sweeps, and the C ABI of include/bem.h.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+
+#include "bem.h"
+#include "bem_impl.h"
+
+namespace bem {
+template <typename T> void set_smem_attrs();
+}
+
+using namespace bem;
+
+static thread_local std::string g_err;
+
+static int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+static int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CK(call)                                                                                \
+  do {                                                                                          \
+    cudaError_t e_ = (call);                                                                    \
+    if (e_ != cudaSuccess)                                                                      \
+      return fail(e_ == cudaErrorMemoryAllocation ? BEM_ENOMEM : BEM_ECUDA, "%s: %s (%s:%d)",   \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                           \
+  } while (0)
+
+#define CKR(call)                  \
+  do {                             \
+    int r_ = (call);               \
+    if (r_ != BEM_OK) return r_;   \
+  } while (0)
+
+namespace {
+
+constexpr int kChunk = 8;  // CG iterations per captured graph launch
+
+template <typename T> struct PrecFields {
+  T *p = nullptr, *g = nullptr, *t = nullptr, *r = nullptr, *c = nullptr;
+  bool ready = false;
+  cudaGraphExec_t pk_graph[2] = {nullptr, nullptr}, cg_graph[2] = {nullptr, nullptr};  // [timed]
+};
+
+int ilog2(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
+int pow2_at_least(int v) { int p = 1; while (p < v) p <<= 1; return p; }
+
+Plan make_plan(int nx, int ny, int px, int py, int esize) {
+  Plan pl{};
+  pl.nx = nx; pl.ny = ny; pl.px = px; pl.py = py;
+  pl.M = px / 2; pl.logM = ilog2(pl.M); pl.logPy = ilog2(py);
+  const int tr = pl.M / 8;
+  int nb = 256 / tr;
+  const int sector = 32 / (2 * esize);
+  if (nb < sector) nb = sector;
+  if (nb < 1) nb = 1;
+  while (nb > 1 && nb * tr > 1024) nb >>= 1;
+  while (nb > 1 && (size_t)nb * (pl.M + 1) * 2 * esize > 128 * 1024) nb >>= 1;
+  pl.nbA = nb;
+  pl.threadsA = nb * tr;
+  pl.gridA = (ny + nb - 1) / nb;
+  pl.smemA = (size_t)nb * pl.M * 2 * esize;
+  pl.smemC = (size_t)nb * (pl.M + 1) * 2 * esize;
+  const int tb = py / 8;
+  int nbb = 256 / tb;
+  if (nbb < 1) nbb = 1;
+  while (nbb > 1 && (size_t)nbb * py * 2 * esize > 128 * 1024) nbb >>= 1;
+  pl.nbB = nbb;
+  pl.threadsB = nbb * tb;
+  pl.gridB = (pl.M + nbb - 1) / nbb;
+  pl.smemB = (size_t)nbb * py * 2 * esize;
+  return pl;
+}
+
+}  // namespace
+
+struct bem_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  Plan plan32{}, plan64{};
+  int nx = 0, ny = 0, px = 0, py = 0;
+  double dx = 0, dy = 0, k = 0, nu = 0, E0 = 0, c0 = 0, alpha = 0, A = 0;
+  double* kq64 = nullptr;
+  double* khat64 = nullptr;
+  float* khat32 = nullptr;
+  void* W = nullptr;
+  double* h64 = nullptr;    // profile
+  double* io64 = nullptr;   // FP64 staging / FP64 pressure of the refinement
+  double* io64b = nullptr;  // second FP64 staging
+  uint8_t* S = nullptr;
+  double* part = nullptr;   // per-CTA partials (A)
+  double* partC = nullptr;  // per-CTA partials (C)
+  double* partE = nullptr;  // per-CTA partials (elementwise kernels)
+  double* stats = nullptr;  // 4 doubles + stats partials
+  int stats_ngrid = 0;
+  int ew_ngrid = 0;
+  Scalars* sc = nullptr;
+  Scalars* sc_host = nullptr;  // pinned
+  double* stats_host = nullptr;  // pinned
+  PrecFields<float> f32;
+  PrecFields<double> f64;
+  size_t bytes = 0;
+  unsigned long long launches = 0;
+  bool timing = false;          // BEM_FLAG_TIME_PASSES for the current call
+  cudaEvent_t ev[2][4] = {};    // [pk/cg][A start, B start, C start, C end]
+  double pass_ms[3] = {0, 0, 0};
+  long long pass_count[2] = {0, 0};
+};
+
+namespace {
+
+template <typename T> PrecFields<T>& fields_of(bem_ctx* h);
+template <> PrecFields<float>& fields_of<float>(bem_ctx* h) { return h->f32; }
+template <> PrecFields<double>& fields_of<double>(bem_ctx* h) { return h->f64; }
+template <typename T> const Plan& plan_of(bem_ctx* h);
+template <> const Plan& plan_of<float>(bem_ctx* h) { return h->plan32; }
+template <> const Plan& plan_of<double>(bem_ctx* h) { return h->plan64; }
+template <typename T> const T* khat_of(bem_ctx* h);
+template <> const float* khat_of<float>(bem_ctx* h) { return h->khat32; }
+template <> const double* khat_of<double>(bem_ctx* h) { return h->khat64; }
+
+int dmalloc(bem_ctx* h, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(BEM_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+  }
+  h->bytes += bytes;
+  return BEM_OK;
+}
+
+template <typename T>
+int ensure_fields(bem_ctx* h) {
+  PrecFields<T>& f = fields_of<T>(h);
+  if (f.ready) return BEM_OK;
+  const size_t n = (size_t)h->nx * h->ny;
+  CKR(dmalloc(h, (void**)&f.p, n * sizeof(T)));
+  CKR(dmalloc(h, (void**)&f.g, n * sizeof(T)));
+  CKR(dmalloc(h, (void**)&f.t, n * sizeof(T)));
+  CKR(dmalloc(h, (void**)&f.r, n * sizeof(T)));
+  CKR(dmalloc(h, (void**)&f.c, n * sizeof(T)));
+  CK(cudaMemsetAsync(f.p, 0, n * sizeof(T), h->stream));
+  CK(cudaMemsetAsync(f.g, 0, n * sizeof(T), h->stream));
+  CK(cudaMemsetAsync(f.t, 0, n * sizeof(T), h->stream));
+  CK(cudaMemsetAsync(f.r, 0, n * sizeof(T), h->stream));
+  f.ready = true;
+  return BEM_OK;
+}
+
+template <typename T>
+PassArgs<T> make_args(bem_ctx* h) {
+  PassArgs<T> a{};
+  a.pl = plan_of<T>(h);
+  PrecFields<T>& pf = fields_of<T>(h);
+  a.f.p = pf.p; a.f.g = pf.g; a.f.t = pf.t; a.f.r = pf.r; a.f.c = pf.c; a.f.S = h->S;
+  a.W = h->W;
+  a.rows_w = h->ny;
+  a.nrows_in = h->ny;
+  a.ncols_in = h->nx;
+  a.khat = khat_of<T>(h);
+  a.uscale = h->A / ((double)h->px * (double)h->py);
+  a.partA = h->part;
+  a.partC = h->partC;
+  a.sc = h->sc;
+  return a;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Copy n doubles from a host or device pointer to the device buffer dst.
+int upload(bem_ctx* h, double* dst, const double* src, size_t n) {
+  CK(cudaMemcpyAsync(dst, src, n * sizeof(double),
+                     is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                     h->stream));
+  return BEM_OK;
+}
+int download(bem_ctx* h, double* dst, const double* src, size_t n) {
+  CK(cudaMemcpyAsync(dst, src, n * sizeof(double),
+                     is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     h->stream));
+  return BEM_OK;
+}
+
+int read_scalars(bem_ctx* h) {
+  CK(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return BEM_OK;
+}
+
+int init_scalars(bem_ctx* h, double tol, int max_iter, double pcrit) {
+  Scalars s{};
+  s.tol = tol;
+  s.max_iter = max_iter;
+  s.G_old = 1.0;
+  s.delta = 0.0;
+  s.bnorm = 1.0;
+  s.pcrit = pcrit;
+  *h->sc_host = s;
+  CK(cudaMemcpyAsync(h->sc, h->sc_host, sizeof(Scalars), cudaMemcpyHostToDevice, h->stream));
+  // the host copy is reused for reads; make sure the upload has consumed it
+  CK(cudaStreamSynchronize(h->stream));
+  return BEM_OK;
+}
+
+// u = A K*x for one field of type T (x -> dst), plain passes.
+template <typename T>
+void conv_plain(bem_ctx* h, const T* x, T* dst, cudaStream_t s) {
+  PassArgs<T> a = make_args<T>(h);
+  a.f.src = x;
+  a.f.dst = dst;
+  a.sc = nullptr;
+  launch_pass_a<T>(a, A_PLAIN, s);
+  launch_pass_b<T>(a, B_CONV, s);
+  launch_pass_c<T>(a, C_PLAIN, s);
+  h->launches += 3;
+}
+
+template <typename T>
+int capture(bem_ctx* h, bool pk, bool timed, cudaGraphExec_t* out) {
+  cudaGraph_t graph;
+  cudaEvent_t* ev = h->ev[pk ? 0 : 1];
+  if (timed && !ev[0])
+    for (int i = 0; i < 4; ++i) CK(cudaEventCreate(&ev[i]));
+  CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  PassArgs<T> a = make_args<T>(h);
+  Fields<T> f = a.f;
+  for (int it = 0; it < kChunk; ++it) {
+    const bool mark = timed && it == 0;
+    if (mark) cudaEventRecord(ev[0], h->stream);
+    launch_pass_a<T>(a, pk ? A_PK_P : A_CG_T, h->stream);
+    if (mark) cudaEventRecord(ev[1], h->stream);
+    launch_pass_b<T>(a, B_CONV, h->stream);
+    if (mark) cudaEventRecord(ev[2], h->stream);
+    launch_pass_c<T>(a, pk ? C_PK_G : C_CG_R, h->stream);
+    if (mark) cudaEventRecord(ev[3], h->stream);
+    if (pk) {
+      launch_pass_a<T>(a, A_PK_T, h->stream);
+      launch_pass_b<T>(a, B_CONV, h->stream);
+      launch_pass_c<T>(a, C_PK_R, h->stream);
+    } else {
+      launch_cg_update<T>(a.pl, f, h->partE, h->sc, h->ew_ngrid, h->stream);
+    }
+  }
+  cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+  if (e != cudaSuccess) return fail(BEM_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(BEM_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+  return BEM_OK;
+}
+
+// Run chunks of the captured loop until the device sets `done`.
+int run_loop(bem_ctx* h, cudaGraphExec_t g, int max_iter, bool pk) {
+  const int max_launch = max_iter / kChunk + 2;
+  for (int l = 0; l < max_launch; ++l) {
+    CK(cudaGraphLaunch(g, h->stream));
+    h->launches += (unsigned long long)kChunk * (pk ? 6 : 4);
+    CKR(read_scalars(h));
+    if (h->timing) {
+      cudaEvent_t* ev = h->ev[pk ? 0 : 1];
+      for (int i = 0; i < 3; ++i) {
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
+        h->pass_ms[i] += ms;
+      }
+      h->pass_count[0] += 1;
+      if (!pk) h->pass_count[1] += 1;
+    }
+    if (h->sc_host->done) return BEM_OK;
+  }
+  return BEM_OK;
+}
+
+struct StepOut {
+  int iterations = 0;
+  double eps = 0;
+  int status = BEM_OK;
+};
+
+int map_status(int sc_status) {
+  if (sc_status == SC_NOCONV) return BEM_ENOCONV;
+  if (sc_status == SC_NUMERIC) return BEM_ENUMERIC;
+  return BEM_OK;
+}
+
+// Non-adhesive solve at depth d in precision T (Sec. 2.1, Polonsky-Keer CG).
+template <typename T>
+int run_pk(bem_ctx* h, double d, double tol, int max_iter, bool warm, StepOut* so) {
+  CKR(ensure_fields<T>(h));
+  PrecFields<T>& pf = fields_of<T>(h);
+  const int tg = h->timing ? 1 : 0;
+  if (!pf.pk_graph[tg]) CKR(capture<T>(h, true, h->timing, &pf.pk_graph[tg]));
+  launch_pk_init<T>(plan_of<T>(h), h->h64, d, pf.c, pf.p, pf.t, warm ? 1 : 0, h->ew_ngrid, h->stream);
+  h->launches += 1;
+  CKR(init_scalars(h, tol, max_iter, 0.0));
+  CKR(run_loop(h, pf.pk_graph[tg], max_iter, true));
+  so->iterations += h->sc_host->iter;
+  so->eps = h->sc_host->eps;
+  if (h->sc_host->status != SC_OK) so->status = map_status(h->sc_host->status);
+  return BEM_OK;
+}
+
+// Fixed-set CG: A (K x)_S + c_S = 0, x = 0 off S, from the current x = f.p.
+template <typename T>
+int run_fixed_cg(bem_ctx* h, double tol, int max_iter, double pcrit, StepOut* so) {
+  CKR(ensure_fields<T>(h));
+  PrecFields<T>& pf = fields_of<T>(h);
+  const int tg = h->timing ? 1 : 0;
+  if (!pf.cg_graph[tg]) CKR(capture<T>(h, false, h->timing, &pf.cg_graph[tg]));
+  CKR(init_scalars(h, tol, max_iter, pcrit));
+  const size_t n = (size_t)h->nx * h->ny;
+  launch_mask_field<T>(pf.p, h->S, n, h->stream);
+  launch_mask_field<T>(pf.t, h->S, n, h->stream);
+  PassArgs<T> a = make_args<T>(h);
+  a.f.src = pf.p;
+  launch_pass_a<T>(a, A_PLAIN, h->stream);
+  launch_pass_b<T>(a, B_CONV, h->stream);
+  launch_pass_c<T>(a, C_CG_G, h->stream);
+  h->launches += 5;
+  CKR(read_scalars(h));
+  if (!h->sc_host->done) CKR(run_loop(h, pf.cg_graph[tg], max_iter, false));
+  so->iterations += h->sc_host->iter;
+  so->eps = h->sc_host->eps;
+  if (h->sc_host->status != SC_OK) so->status = map_status(h->sc_host->status);
+  return BEM_OK;
+}
+
+template <typename T>
+int detach(bem_ctx* h, double pcrit, double* ndetached) {
+  PrecFields<T>& pf = fields_of<T>(h);
+  Fields<T> f{};
+  f.p = pf.p;
+  f.S = h->S;
+  h->sc_host->pcrit = pcrit;
+  CK(cudaMemcpyAsync(&h->sc->pcrit, &pcrit, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  launch_detach<T>(plan_of<T>(h), f, h->partE, h->sc, h->ew_ngrid, h->stream);
+  h->launches += 1;
+  CKR(read_scalars(h));
+  *ndetached = h->sc_host->n_ol;
+  return BEM_OK;
+}
+
+template <typename T>
+int collect(bem_ctx* h, const T* p, const T* g, int use_set, bem_result* r) {
+  launch_stats<T>(plan_of<T>(h), p, g, h->S, use_set, h->stats + 8, h->stats, h->stats_ngrid,
+                  h->stream);
+  h->launches += 1;
+  CK(cudaMemcpyAsync(h->stats_host, h->stats, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  const double cell = h->dx * h->dy;
+  r->force = cell * h->stats_host[0];
+  r->contact_count = (int)h->stats_host[1];
+  r->area = cell * h->stats_host[1];
+  r->contact_radius = sqrt(r->area / 3.14159265358979323846);
+  r->max_gap_violation = fmax(h->stats_host[2], h->stats_host[3]);
+  return BEM_OK;
+}
+
+// FP64 gap of the FP64 pressure in io64: g64 = A K p64 + h - d  (into f64.g).
+int gap64(bem_ctx* h, double d) {
+  CKR(ensure_fields<double>(h));
+  PrecFields<double>& f = h->f64;
+  const size_t n = (size_t)h->nx * h->ny;
+  launch_offset<double>(h->h64, d, f.c, n, h->stream);
+  PassArgs<double> a = make_args<double>(h);
+  a.f.src = h->io64;
+  a.sc = nullptr;
+  launch_pass_a<double>(a, A_PLAIN, h->stream);
+  launch_pass_b<double>(a, B_CONV, h->stream);
+  launch_pass_c<double>(a, C_GAP, h->stream);
+  h->launches += 4;
+  return BEM_OK;
+}
+
+// Largest |x| over S (use_set) -- via the statistics kernel.
+int max_abs_on_set(bem_ctx* h, const double* x, double* out) {
+  bem_result tmp{};
+  CKR(collect<double>(h, h->io64, x, 1, &tmp));
+  *out = h->stats_host[2];
+  return BEM_OK;
+}
+
+// FP64-residual refinement of the FP32 solution (precision BEM_PREC_FP32_REFINE).
+// io64 holds the FP64 pressure.  Each sweep computes the FP64 gap g64 of it
+// (one FP64 convolution), chooses the set S, solves A K dp + g64 = 0 on S with
+// the FP32 fixed-set CG, and adds dp.  Non-adhesive: S = {p > 0} U {g < 0} and
+// p is projected onto p >= 0 after the update; adhesive: S is held and tension
+// is allowed.  Stops when max_S |g64| <= tol64 * max_S |h - d|.
+int refine(bem_ctx* h, double d, bool adhesive, int sweeps, double tol64, StepOut* so) {
+  const size_t n = (size_t)h->nx * h->ny;
+  for (int s = 0; s < sweeps; ++s) {
+    CKR(gap64(h, d));
+    if (!adhesive) { launch_active_set(h->io64, h->f64.g, h->S, n, h->stream); h->launches += 1; }
+    double res = 0, scale = 0;
+    CKR(max_abs_on_set(h, h->f64.g, &res));
+    CKR(max_abs_on_set(h, h->f64.c, &scale));
+    if (res <= tol64 * scale) break;
+    launch_to_f32(h->f64.g, h->f32.c, n, h->stream);
+    h->launches += 1;
+    CK(cudaMemsetAsync(h->f32.p, 0, n * sizeof(float), h->stream));
+    CK(cudaMemsetAsync(h->f32.t, 0, n * sizeof(float), h->stream));
+    StepOut cg;
+    CKR(run_fixed_cg<float>(h, 1e-6, 2000, 0.0, &cg));
+    so->iterations += cg.iterations;
+    launch_refine_apply(h->io64, h->f32.p, h->S, adhesive ? 0 : 1, n, h->stream);
+    h->launches += 1;
+  }
+  return BEM_OK;
+}
+
+int validate_ptr(const void* p, const char* name) {
+  if (!p) return fail(BEM_EINVAL, "%s must not be NULL", name);
+  return BEM_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+
+extern "C" const char* bem_last_error(void) { return g_err.c_str(); }
+
+extern "C" int bem_create(int Nx, int Ny, double dx, double dy, double k, double nu, double E0,
+                          double c0, bem_handle* out) {
+  g_err.clear();
+  if (!out) return fail(BEM_EINVAL, "out must not be NULL");
+  if (Nx < 2 || Ny < 2 || Nx > 4096 || Ny > 4096)
+    return fail(BEM_EINVAL, "grid %dx%d outside 2..4096", Nx, Ny);
+  if (!(dx > 0) || !(dy > 0)) return fail(BEM_EINVAL, "element sizes must be > 0");
+  if (!(k > -1.0 && k < 1.0)) return fail(BEM_EINVAL, "k=%g outside (-1, 1)", k);
+  if (!(nu > -1.0 && nu <= 0.5)) return fail(BEM_EINVAL, "nu=%g outside (-1, 0.5]", nu);
+  if (!(E0 > 0) || !(c0 > 0)) return fail(BEM_EINVAL, "E0 and c0 must be > 0");
+  const double alpha = bem_alpha(k, nu);
+  if (!(alpha > 0) || !isfinite(alpha)) return fail(BEM_EINVAL, "alpha(k=%g, nu=%g) undefined (beta^2 <= 0)", k, nu);
+
+  bem_ctx* h = new bem_ctx();
+  auto cleanup = [&](int rc) { bem_destroy(h); return rc; };
+  if (cudaGetDevice(&h->device) != cudaSuccess) return cleanup(fail(BEM_ECUDA, "no CUDA device"));
+  if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess)
+    return cleanup(fail(BEM_ECUDA, "stream creation failed"));
+  static bool attrs_done = false;
+  if (!attrs_done) {
+    set_smem_attrs<float>();
+    set_smem_attrs<double>();
+    if (influence_init_nodes() != 0) return cleanup(fail(BEM_ECUDA, "quadrature nodes upload failed"));
+    attrs_done = true;
+  }
+  h->nx = Nx; h->ny = Ny; h->dx = dx; h->dy = dy; h->k = k; h->nu = nu; h->E0 = E0; h->c0 = c0;
+  h->alpha = alpha;
+  h->A = alpha * (1.0 - nu * nu) * pow(c0, k) / E0;  // Eq. 12
+  h->px = pow2_at_least(2 * Nx < 16 ? 16 : 2 * Nx);
+  h->py = pow2_at_least(2 * Ny < 16 ? 16 : 2 * Ny);
+  h->plan32 = make_plan(Nx, Ny, h->px, h->py, 4);
+  h->plan64 = make_plan(Nx, Ny, h->px, h->py, 8);
+  const int M = h->px / 2, hyq = h->py / 2 + 1;
+  const size_t n = (size_t)Nx * Ny;
+  int rc;
+  if ((rc = dmalloc(h, (void**)&h->kq64, sizeof(double) * (size_t)hyq * (M + 1)))) return cleanup(rc);
+  if ((rc = dmalloc(h, (void**)&h->khat64, sizeof(double) * (size_t)hyq * (M + 1)))) return cleanup(rc);
+  if ((rc = dmalloc(h, (void**)&h->khat32, sizeof(float) * (size_t)hyq * (M + 1)))) return cleanup(rc);
+  if ((rc = dmalloc(h, &h->W, sizeof(double) * 2 * (size_t)(M + 1) * Ny))) return cleanup(rc);
+  if ((rc = dmalloc(h, (void**)&h->h64, sizeof(double) * n))) return cleanup(rc);
+  if ((rc = dmalloc(h, (void**)&h->io64, sizeof(double) * n))) return cleanup(rc);
+  if ((rc = dmalloc(h, (void**)&h->io64b, sizeof(double) * n))) return cleanup(rc);
+  if ((rc = dmalloc(h, (void**)&h->S, n))) return cleanup(rc);
+  const int gmax = (h->plan32.gridA > h->plan64.gridA ? h->plan32.gridA : h->plan64.gridA);
+  if ((rc = dmalloc(h, (void**)&h->part, sizeof(double) * 4 * (size_t)gmax))) return cleanup(rc);
+  if ((rc = dmalloc(h, (void**)&h->partC, sizeof(double) * 4 * (size_t)gmax))) return cleanup(rc);
+  h->ew_ngrid = (int)((n + 255) / 256 < 152 * 8 ? (n + 255) / 256 : 152 * 8);
+  if (h->ew_ngrid < 1) h->ew_ngrid = 1;
+  if ((rc = dmalloc(h, (void**)&h->partE, sizeof(double) * 4 * (size_t)h->ew_ngrid))) return cleanup(rc);
+  h->stats_ngrid = h->ew_ngrid;
+  if ((rc = dmalloc(h, (void**)&h->stats, sizeof(double) * (8 + 4 * (size_t)h->stats_ngrid + 8)))) return cleanup(rc);
+  if ((rc = dmalloc(h, (void**)&h->sc, sizeof(Scalars)))) return cleanup(rc);
+  if (cudaMallocHost((void**)&h->sc_host, sizeof(Scalars)) != cudaSuccess ||
+      cudaMallocHost((void**)&h->stats_host, 8 * sizeof(double)) != cudaSuccess)
+    return cleanup(fail(BEM_ENOMEM, "pinned allocation failed"));
+  if (cudaMemsetAsync(h->sc, 0, sizeof(Scalars), h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->stats, 0, sizeof(double) * (8 + 4 * (size_t)h->stats_ngrid + 8), h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->S, 0, n, h->stream) != cudaSuccess)
+    return cleanup(fail(BEM_ECUDA, "memset failed"));
+
+  // a1: influence coefficients on the offsets 0..Px/2, 0..Py/2 (Eq. 9)
+  launch_influence(h->kq64, M + 1, hyq, dx, dy, k, h->stream);
+  // spectrum of the even torus extension (Eq. 13: FFT(K)), FP64, once
+  {
+    void* Wspec = nullptr;
+    if (cudaMalloc(&Wspec, sizeof(double) * 2 * (size_t)(M + 1) * h->py) != cudaSuccess)
+      return cleanup(fail(BEM_ENOMEM, "spectrum workspace allocation failed"));
+    PassArgs<double> a{};
+    a.pl = h->plan64;
+    a.W = Wspec;
+    a.rows_w = h->py;
+    a.nrows_in = h->py;
+    a.ncols_in = h->px;
+    a.kq64 = h->kq64;
+    a.khat64_out = h->khat64;
+    a.khat32_out = h->khat32;
+    launch_pass_a<double>(a, A_TORUS, h->stream);
+    launch_pass_b<double>(a, B_SPECTRUM, h->stream);
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    cudaFree(Wspec);
+    if (e != cudaSuccess) return cleanup(fail(BEM_ECUDA, "spectrum set-up failed: %s", cudaGetErrorString(e)));
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cleanup(fail(BEM_ECUDA, "set-up kernels failed: %s", cudaGetErrorString(e)));
+  *out = h;
+  return BEM_OK;
+}
+
+extern "C" void bem_destroy(bem_handle h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  auto fr = [](void* p) { if (p) cudaFree(p); };
+  for (int t = 0; t < 2; ++t)
+    for (cudaGraphExec_t g : {h->f32.pk_graph[t], h->f32.cg_graph[t], h->f64.pk_graph[t], h->f64.cg_graph[t]})
+      if (g) cudaGraphExecDestroy(g);
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 4; ++j)
+      if (h->ev[i][j]) cudaEventDestroy(h->ev[i][j]);
+  fr(h->kq64); fr(h->khat64); fr(h->khat32); fr(h->W); fr(h->h64); fr(h->io64); fr(h->io64b);
+  fr(h->S); fr(h->part); fr(h->partC); fr(h->partE); fr(h->stats); fr(h->sc);
+  fr(h->f32.p); fr(h->f32.g); fr(h->f32.t); fr(h->f32.r); fr(h->f32.c);
+  fr(h->f64.p); fr(h->f64.g); fr(h->f64.t); fr(h->f64.r); fr(h->f64.c);
+  if (h->sc_host) cudaFreeHost(h->sc_host);
+  if (h->stats_host) cudaFreeHost(h->stats_host);
+  if (h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+extern "C" int bem_get_info(bem_handle h, bem_info* info) {
+  if (!h || !info) return fail(BEM_EINVAL, "NULL argument");
+  info->Nx = h->nx; info->Ny = h->ny; info->Px = h->px; info->Py = h->py;
+  info->dx = h->dx; info->dy = h->dy; info->k = h->k; info->nu = h->nu; info->E0 = h->E0; info->c0 = h->c0;
+  info->alpha = h->alpha; info->compliance = h->A; info->device_bytes = h->bytes;
+  info->kernel_launches = h->launches;
+  return BEM_OK;
+}
+
+extern "C" int bem_pass_times(bem_handle h, double ms[3], long long count[2], int reset) {
+  if (!h || !ms || !count) return fail(BEM_EINVAL, "NULL argument");
+  for (int i = 0; i < 3; ++i) ms[i] = h->pass_ms[i];
+  count[0] = h->pass_count[0];
+  count[1] = h->pass_count[1];
+  if (reset) {
+    for (int i = 0; i < 3; ++i) h->pass_ms[i] = 0;
+    h->pass_count[0] = h->pass_count[1] = 0;
+  }
+  return BEM_OK;
+}
+
+extern "C" int bem_influence_table(bem_handle h, double* out) {
+  if (!h) return fail(BEM_EINVAL, "NULL handle");
+  CKR(validate_ptr(out, "out"));
+  const size_t cnt = (size_t)(h->px / 2 + 1) * (h->py / 2 + 1);
+  CKR(download(h, out, h->kq64, cnt));
+  CK(cudaStreamSynchronize(h->stream));
+  return BEM_OK;
+}
+
+__global__ void k_transpose_quarter(const double* src, double* dst, int hx, int hyq) {
+  // src[kx*hyq + ky] -> dst[ky*hx + kx]
+  const int kx = blockIdx.x * blockDim.x + threadIdx.x, ky = blockIdx.y;
+  if (kx < hx && ky < hyq) dst[(size_t)ky * hx + kx] = src[(size_t)kx * hyq + ky];
+}
+
+extern "C" int bem_spectrum(bem_handle h, double* out) {
+  if (!h) return fail(BEM_EINVAL, "NULL handle");
+  CKR(validate_ptr(out, "out"));
+  const int hx = h->px / 2 + 1, hyq = h->py / 2 + 1;
+  double* tmp = nullptr;
+  CK(cudaMallocAsync((void**)&tmp, sizeof(double) * (size_t)hx * hyq, h->stream));
+  k_transpose_quarter<<<dim3((hx + 127) / 128, hyq), 128, 0, h->stream>>>(h->khat64, tmp, hx, hyq);
+  int rc = download(h, out, tmp, (size_t)hx * hyq);
+  cudaFreeAsync(tmp, h->stream);
+  CK(cudaStreamSynchronize(h->stream));
+  return rc;
+}
+
+extern "C" int bem_convolve(bem_handle h, int precision, const double* p, double* u) {
+  if (!h) return fail(BEM_EINVAL, "NULL handle");
+  CKR(validate_ptr(p, "p"));
+  CKR(validate_ptr(u, "u"));
+  const size_t n = (size_t)h->nx * h->ny;
+  CKR(upload(h, h->io64, p, n));
+  if (precision == BEM_PREC_FP64) {
+    conv_plain<double>(h, h->io64, h->io64b, h->stream);
+  } else if (precision == BEM_PREC_FP32) {
+    CKR(ensure_fields<float>(h));
+    launch_convert_in<float>(h->io64, h->f32.p, n, h->stream);
+    conv_plain<float>(h, h->f32.p, h->f32.g, h->stream);
+    launch_convert_out<float>(h->f32.g, h->io64b, n, h->stream);
+  } else {
+    return fail(BEM_EINVAL, "precision %d not supported by bem_convolve", precision);
+  }
+  CKR(download(h, u, h->io64b, n));
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaGetLastError());
+  return BEM_OK;
+}
+
+namespace {
+
+struct SolveCfg {
+  int precision = BEM_PREC_FP32;
+  double tol = 0;
+  int max_iter = 20000;
+  int sweeps = 3;
+  int flags = 0;
+  cudaStream_t user = nullptr;
+};
+
+int parse_opts(const bem_opts* o, SolveCfg* c) {
+  if (o) {
+    if (o->precision < BEM_PREC_FP64 || o->precision > BEM_PREC_FP32_REFINE)
+      return fail(BEM_EINVAL, "unknown precision %d", o->precision);
+    if (o->tol < 0 || o->max_iter < 0 || o->refine_sweeps < 0)
+      return fail(BEM_EINVAL, "negative option");
+    c->precision = o->precision;
+    c->tol = o->tol;
+    if (o->max_iter > 0) c->max_iter = o->max_iter;
+    if (o->refine_sweeps > 0) c->sweeps = o->refine_sweeps;
+    c->user = (cudaStream_t)o->stream;
+    c->flags = o->flags;
+  }
+  if (c->tol == 0) c->tol = c->precision == BEM_PREC_FP64 ? 1e-10 : 1e-6;
+  return BEM_OK;
+}
+
+// One non-adhesive step in the configured precision; leaves the FP64 pressure
+// in io64 and fills r.
+int step_nonadhesive(bem_ctx* h, const SolveCfg& cfg, double d, bool warm, bem_result* r) {
+  const size_t n = (size_t)h->nx * h->ny;
+  StepOut so;
+  if (cfg.precision == BEM_PREC_FP64) {
+    CKR(run_pk<double>(h, d, cfg.tol, cfg.max_iter, warm, &so));
+    CKR(collect<double>(h, h->f64.p, h->f64.g, 0, r));
+    CK(cudaMemcpyAsync(h->io64, h->f64.p, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  } else {
+    CKR(run_pk<float>(h, d, cfg.tol, cfg.max_iter, warm, &so));
+    launch_convert_out<float>(h->f32.p, h->io64, n, h->stream);
+    h->launches += 1;
+    if (cfg.precision == BEM_PREC_FP32_REFINE) {
+      CKR(refine(h, d, false, cfg.sweeps, 1e-13, &so));
+      CKR(gap64(h, d));
+      CKR(collect<double>(h, h->io64, h->f64.g, 0, r));
+      // keep the FP32 warm start in step with the refined pressure
+      launch_to_f32(h->io64, h->f32.p, n, h->stream);
+      h->launches += 1;
+    } else {
+      CKR(collect<float>(h, h->f32.p, h->f32.g, 0, r));
+    }
+  }
+  r->iterations = so.iterations;
+  r->final_eps = so.eps;
+  r->detach_rounds = 0;
+  r->status = so.status;
+  r->depth = d;
+  return BEM_OK;
+}
+
+// One adhesive pull-off step at depth d on the current set S (Sec. 3.1).
+template <typename T>
+int step_adhesive_t(bem_ctx* h, const SolveCfg& cfg, double d, double pcrit, bem_result* r) {
+  const size_t n = (size_t)h->nx * h->ny;
+  PrecFields<T>& pf = fields_of<T>(h);
+  StepOut so;
+  int rounds = 0;
+  launch_offset<T>(h->h64, d, pf.c, n, h->stream);
+  h->launches += 1;
+  const double tol = cfg.precision == BEM_PREC_FP64 ? 1e-12 : cfg.tol;
+  for (;;) {
+    CKR(run_fixed_cg<T>(h, tol, cfg.max_iter, pcrit, &so));
+    if (cfg.precision == BEM_PREC_FP32_REFINE) {
+      launch_convert_out<float>(h->f32.p, h->io64, n, h->stream);
+      CKR(refine(h, d, true, cfg.sweeps, 1e-13, &so));
+      launch_to_f32(h->io64, h->f32.p, n, h->stream);
+      launch_offset<float>(h->h64, d, h->f32.c, n, h->stream);
+      h->launches += 3;
+    }
+    double nd = 0;
+    CKR(detach<T>(h, pcrit, &nd));
+    if (nd == 0) break;
+    ++rounds;
+  }
+  // true gap of the final state (for the off-contact check)
+  if (cfg.precision == BEM_PREC_FP32_REFINE) {
+    // io64 holds the refined pressure; the last round detached nothing
+    CKR(gap64(h, d));
+    CKR(collect<double>(h, h->io64, h->f64.g, 1, r));
+  } else {
+    PassArgs<T> a = make_args<T>(h);
+    a.f.src = pf.p;
+    a.sc = nullptr;
+    launch_offset<T>(h->h64, d, pf.c, n, h->stream);
+    launch_pass_a<T>(a, A_PLAIN, h->stream);
+    launch_pass_b<T>(a, B_CONV, h->stream);
+    launch_pass_c<T>(a, C_GAP, h->stream);
+    CKR(collect<T>(h, pf.p, pf.g, 1, r));
+    launch_convert_out<T>(pf.p, h->io64, n, h->stream);
+    h->launches += 5;
+  }
+  r->iterations = so.iterations;
+  r->final_eps = so.eps;
+  r->detach_rounds = rounds;
+  r->status = so.status;
+  r->depth = d;
+  return BEM_OK;
+}
+
+int run_sweep(bem_ctx* h, const double* profile, const double* d_steps, int nsteps, double dgamma,
+              const bem_opts* opts, bem_result* per_step, double* final_pressure) {
+  g_err.clear();
+  if (!h) return fail(BEM_EINVAL, "NULL handle");
+  CKR(validate_ptr(profile, "profile"));
+  CKR(validate_ptr(d_steps, "d_steps"));
+  CKR(validate_ptr(per_step, "per_step"));
+  if (nsteps < 1) return fail(BEM_EINVAL, "nsteps must be >= 1");
+  SolveCfg cfg;
+  CKR(parse_opts(opts, &cfg));
+  const bool adhesive = dgamma > 0;
+  for (int i = 0; i < nsteps; ++i)
+    if (!isfinite(d_steps[i])) return fail(BEM_EINVAL, "depth %d is not finite", i);
+  double pcrit = 0;
+  if (adhesive) {
+    if (fabs(h->dx - h->dy) > 1e-12 * h->dx)
+      return fail(BEM_EINVAL, "adhesive contact needs square elements (Eq. 24)");
+    for (int i = 1; i < nsteps; ++i)
+      if (d_steps[i] > d_steps[i - 1]) return fail(BEM_EINVAL, "adhesive depths must not increase");
+    pcrit = bem_p_crit(h->k, h->nu, h->E0, h->c0, dgamma, h->dx);
+    if (!isfinite(pcrit)) return fail(BEM_EINVAL, "p_crit undefined for k=%g (Table 1 covers |k| <= 0.9)", h->k);
+  }
+  const size_t n = (size_t)h->nx * h->ny;
+  h->timing = (cfg.flags & BEM_FLAG_TIME_PASSES) != 0;
+  cudaEvent_t ev = nullptr;
+  if (cfg.user) {
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CK(cudaEventRecord(ev, cfg.user));
+    CK(cudaStreamWaitEvent(h->stream, ev, 0));
+  }
+  CKR(upload(h, h->h64, profile, n));
+  int first_bad = BEM_OK;
+  bool warm = false;  // every sweep starts from the initial guess
+  for (int i = 0; i < nsteps; ++i) {
+    bem_result r{};
+    if (!adhesive || i == 0) {
+      CKR(step_nonadhesive(h, cfg, d_steps[i], warm, &r));
+      warm = r.force > 0;
+      if (adhesive) {
+        if (cfg.precision == BEM_PREC_FP64) launch_set_from_p<double>(h->f64.p, h->S, n, h->stream);
+        else launch_set_from_p<double>(h->io64, h->S, n, h->stream);
+        if (cfg.precision != BEM_PREC_FP64) launch_to_f32(h->io64, h->f32.p, n, h->stream);
+        h->launches += 2;
+      }
+    } else {
+      if (cfg.precision == BEM_PREC_FP64) CKR(step_adhesive_t<double>(h, cfg, d_steps[i], pcrit, &r));
+      else CKR(step_adhesive_t<float>(h, cfg, d_steps[i], pcrit, &r));
+    }
+    per_step[i] = r;
+    if (r.status != BEM_OK && first_bad == BEM_OK) first_bad = r.status;
+    if (r.status == BEM_ENUMERIC) break;
+  }
+  if (final_pressure) CKR(download(h, final_pressure, h->io64, n));
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaGetLastError());
+  if (ev) {
+    CK(cudaEventRecord(ev, h->stream));
+    CK(cudaStreamWaitEvent(cfg.user, ev, 0));
+    cudaEventDestroy(ev);
+  }
+  if (first_bad != BEM_OK) fail(first_bad, "solve finished with status %d", first_bad);
+  return first_bad;
+}
+
+}  // namespace
+
+extern "C" int bem_sweep(bem_handle h, const double* profile, const double* d_steps, int nsteps,
+                         double dgamma, const bem_opts* opts, bem_result* per_step,
+                         double* final_pressure) {
+  return run_sweep(h, profile, d_steps, nsteps, dgamma, opts, per_step, final_pressure);
+}
+
+extern "C" int bem_solve(bem_handle h, const double* profile, double d, double dgamma,
+                         double d_preload, const bem_opts* opts, double* pressure_out,
+                         bem_result* res) {
+  if (!res) return fail(BEM_EINVAL, "res must not be NULL");
+  if (dgamma > 0) {
+    if (!(d_preload >= d)) return fail(BEM_EINVAL, "d_preload must be >= d");
+    double ds[2] = {d_preload, d};
+    bem_result rr[2];
+    int rc = run_sweep(h, profile, ds, 2, dgamma, opts, rr, pressure_out);
+    *res = rr[1];
+    res->iterations += rr[0].iterations;
+    return rc;
+  }
+  double ds[1] = {d};
+  return run_sweep(h, profile, ds, 1, 0.0, opts, res, pressure_out);
+}

@@ -31,3 +31,20 @@ def read_golden(name):
             if line and not line.startswith("#"):
                 rows.append([float(x) for x in line.split()])
     return rows
+
+
+@pytest.fixture(scope="session")
+def bem_mod():
+    """The product binding, with the CUDA library built in-tree."""
+    from paper_1612_08395_gb300 import build, bem
+    build.build()
+    bem.load_library()
+    return bem
+
+
+@pytest.fixture(scope="session")
+def cuda_ok():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return True

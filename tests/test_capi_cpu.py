@@ -1,0 +1,78 @@
+"""The C-ABI library without a GPU: it loads, exports every declared entry
+point, its host-only formulas match the oracle, and GPU entry points fail
+cleanly when no device is present."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "bem.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(bem_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("bem_create", "bem_solve", "bem_sweep", "bem_destroy", "bem_last_error",
+                     "bem_convolve", "bem_influence_table", "bem_spectrum"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(bem_mod):
+    lib = bem_mod.load_library()
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+@pytest.mark.parametrize("k", [-0.9, -0.45, 0.0, 0.3, 0.77])
+@pytest.mark.parametrize("nu", [0.0, 0.3, 0.5])
+def test_alpha_matches_oracle(bem_mod, oracle_mod, k, nu):
+    assert bem_mod.alpha(k, nu) == pytest.approx(oracle_mod.alpha(k, nu), rel=1e-13)
+
+
+def test_alpha_invalid_is_nan(bem_mod):
+    assert math.isnan(bem_mod.alpha(1.0, 0.3))
+    assert math.isnan(bem_mod.alpha(0.2, 0.7))
+
+
+def test_c1_corrected_matches_oracle_spline(bem_mod, oracle_mod):
+    for k in np.linspace(-0.9, 0.9, 73):
+        assert bem_mod.c1_corrected(float(k)) == pytest.approx(oracle_mod.c1_corrected(float(k)),
+                                                               rel=1e-12)
+    assert math.isnan(bem_mod.c1_corrected(0.95))
+
+
+def test_table1_values_exact(bem_mod):
+    from conftest import read_golden
+    for k, c in read_golden("table1_c1.txt"):
+        assert bem_mod.c1_corrected(k) == c
+
+
+def test_p_crit_matches_oracle(bem_mod, oracle_mod):
+    for k, nu, g, dl in [(0.3, 0.3, 1e-3, 1 / 2048), (-0.5, 0.25, 1e-2, 1 / 64), (0.65, 0.5, 1e-4, 0.01)]:
+        assert bem_mod.p_crit(k, nu, g, dl) == pytest.approx(oracle_mod.p_crit(k, nu, g, dl), rel=1e-12)
+    assert math.isnan(bem_mod.p_crit(0.3, 0.3, -1.0, 0.1))
+
+
+def test_create_without_gpu_fails_cleanly(bem_mod):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(bem_mod.BemError) as e:
+        bem_mod.Handle(16, 16, 1 / 16, 1 / 16, 0.3, 0.3)
+    assert e.value.code == bem_mod.BEM_ECUDA
+
+
+def test_invalid_parameters_rejected_before_gpu(bem_mod):
+    for args in [(1, 16, 0.1, 0.1, 0.3, 0.3), (16, 16, 0.1, 0.1, 1.0, 0.3),
+                 (16, 16, 0.1, 0.1, 0.3, 0.6), (16, 16, -0.1, 0.1, 0.3, 0.3),
+                 (5000, 16, 0.1, 0.1, 0.3, 0.3)]:
+        with pytest.raises(bem_mod.BemError) as e:
+            bem_mod.Handle(*args)
+        assert e.value.code == bem_mod.BEM_EINVAL
