@@ -1,0 +1,330 @@
+#!/usr/bin/env python3
+"""Benchmark: CG iterations/s of the adhesive 2048 x 2048 load-unload sweep.
+
+Workload (one "step"): graded half-space k = 0.3, nu = 0.3, E0 = c0 = 1, domain
+side 1 on 2048 x 2048 square elements; rigid paraboloid R = 1 centred;
+non-adhesive preload to d0 = +0.02, then 400 adhesive pull-off steps of
+1.1e-4 (to d = -0.024, past pull-off) with work of adhesion 1e-3 (Sec. 3.1
+algorithm, Eq. 24 with Table 1's c1).  FP32 transform passes, FP64 scalars.
+Inputs are synthetic (the paraboloid), resident in HBM for `value`.
+
+value       : CG iterations of all ranks / max-over-ranks device time (CUDA events)
+e2e         : the same through the C ABI with pinned host buffers (profile in,
+              pressure out), wall clock around the call
+roofline    : the dominant transform pass, algorithmic bytes / its live average
+              duration (CUDA events recorded inside the captured CG graphs)
+cpu_baseline: the FP64 oracle (numpy FFT mode) on a bounded sample of the same
+              workload, on this host's cores
+
+--impl reference times the oracle alone (rank 0) and prints its own line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 2048
+K_EXP, NU, E0, C0 = 0.3, 0.3, 1.0, 1.0
+R = 1.0
+DGAMMA = 1e-3
+D0 = 0.02
+DD = 1.1e-4
+NSTEPS = 400
+WORKLOAD = "adhesive paraboloid load-unload 2048x2048 (k=0.3, nu=0.3, R=1, dgamma=1e-3, d0=0.02, 400 steps of 1.1e-4)"
+METRIC = "CG iterations/s, adhesive 2048^2 load-unload sweep"
+UNIT = "iter/s"
+
+
+def d_steps(nsteps=NSTEPS):
+    return np.array([D0] + [D0 - DD * j for j in range(1, nsteps + 1)])
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def pass_bytes(nx, ny, px, py, mode):
+    """Algorithmic HBM bytes of one launch of each transform pass, FP32 fields.
+
+    W (the transposed half spectrum) holds (Px/2+1) x Ny complex64; the
+    spectrum quarter (Px/2+1) x (Py/2+1) float32.  mode 'pk': pass A reads
+    p, t, g and writes p (Polonsky-Keer update); pass C reads c, p and writes
+    g.  mode 'cg': pass A reads S, g, t, writes t; pass C reads S, t, writes r.
+    """
+    n = nx * ny
+    w = 8 * (px // 2 + 1) * ny
+    khat = 4 * (px // 2 + 1) * (py // 2 + 1)
+    if mode == "pk":
+        a = 16 * n + w
+        c = w + 12 * n
+    else:
+        a = 13 * n + w
+        c = w + 9 * n
+    b = 2 * w + khat
+    return {"A": a, "B": b, "C": c}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    per = []
+    for s in range(args.warmup + args.steps):
+        it, el, _ = cpu_oracle_sample_cached(2)
+        if s >= args.warmup:
+            per.append((it, el))
+    its = sum(i for i, _ in per)
+    tot = sum(e for _, e in per)
+    v = its / tot
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (host)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "2 Polonsky-Keer CG iterations of the 2048^2 preload per step "
+                                       "(oracle FFT mode, numpy pocketfft FP64, single thread)"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+_ORACLE_CACHE = {}
+
+
+def cpu_oracle_sample_cached(iters):
+    import oracle
+    from paper_1612_08395_gb300 import inputs
+    if "conv" not in _ORACLE_CACHE:
+        dx = 1.0 / N
+        Kq = oracle.influence_quarter(K_EXP, dx, dx, N + 1, N + 1)
+        _ORACLE_CACHE["conv"] = oracle.FFTConvolver(Kq, N, N)
+    conv = _ORACLE_CACHE["conv"]
+    A = oracle.compliance(K_EXP, NU, E0, C0)
+    h = inputs.paraboloid(N, R)
+    t0 = time.perf_counter()
+    res = oracle.pk_solve(A, conv, h, D0, tol=1e-300, max_iter=iters)
+    return res.iterations, time.perf_counter() - t0, 0.0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_refine", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep-steps", type=int, default=NSTEPS,
+                    help="unloading steps per sweep (400 = the workload; fewer only for profiling)")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    from paper_1612_08395_gb300 import bem, build, inputs
+    build.build()
+    dx = 1.0 / N
+    prof_h = inputs.paraboloid(N, R)
+    prof_d = torch.from_numpy(prof_h).cuda()
+    p_d = torch.empty((N, N), dtype=torch.float64, device="cuda")
+    ds = d_steps(args.sweep_steps)
+    stream = torch.cuda.current_stream()
+    l2_flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    h = bem.Handle(N, N, dx, dx, K_EXP, NU, E0, C0)
+    info = h.info()
+    opts = dict(precision=args.precision, stream=stream)
+
+    def one_step(timed_passes=False):
+        res, rc = h.sweep(prof_d, ds, dgamma=DGAMMA, final_pressure=p_d, time_passes=timed_passes,
+                          **opts)
+        return res
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+
+    # timed region
+    sampler = ClockSampler(local)
+    iters_total = 0
+    launches0 = h.info().kernel_launches
+    h.pass_times(reset=True)
+    step_ms = []
+    results = None
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    for _ in range(args.steps):
+        l2_flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        results = one_step(timed_passes=True)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        iters_total += sum(r.iterations for r in results)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    launches = h.info().kernel_launches - launches0
+    pass_ms, pass_n, pass_cg = h.pass_times(reset=True)
+    elapsed = sum(step_ms) / 1e3
+    el_t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
+    it_t = torch.tensor([float(iters_total)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.barrier()
+        dist.all_reduce(el_t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(it_t, op=dist.ReduceOp.SUM)
+    elapsed_max = float(el_t.item())
+    value = float(it_t.item()) / elapsed_max
+
+    # e2e through the C ABI with pinned host buffers
+    prof_pin = torch.from_numpy(prof_h).pin_memory()
+    out_pin = torch.empty((N, N), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_iters = 0
+    for _ in range(0 if args.no_e2e else args.steps):
+        res, rc = h.sweep(prof_pin, ds, dgamma=DGAMMA, final_pressure=out_pin,
+                          precision=args.precision)
+        e2e_iters += sum(r.iterations for r in res)
+    e2e_s = time.perf_counter() - t0
+    e2e_val = e2e_iters / e2e_s if e2e_iters else None
+
+    # roofline of the dominant pass
+    hbm, peak_src = peaks()
+    avg_ms = [m / max(pass_n, 1) for m in pass_ms]
+    dom = int(np.argmax(avg_ms))
+    names = ["A", "B", "C"]
+    frac_cg = pass_cg / max(pass_n, 1)
+    bpk = pass_bytes(N, N, info.Px, info.Py, "pk")
+    bcg = pass_bytes(N, N, info.Px, info.Py, "cg")
+    bytes_dom = (1 - frac_cg) * bpk[names[dom]] + frac_cg * bcg[names[dom]]
+    achieved = bytes_dom / (avg_ms[dom] * 1e-3) / 1e9
+
+    forces = [r.force for r in results]
+    counts = [r.contact_count for r in results]
+    last_contact = max((i for i, c in enumerate(counts) if c > 0), default=0)
+    if args.sweep_steps != NSTEPS:
+        line_note = f"profiling run: {args.sweep_steps} unloading steps, not the workload"
+    else:
+        line_note = None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * elapsed_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision != "fp64" else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": args.precision, "grid": [N, N],
+                   "torus": [info.Px, info.Py], "parallelism": f"replicas x{world}",
+                   "l2": "flushed between steps (256 MiB write)",
+                   "cg_iterations_per_step": iters_total / args.steps,
+                   "pull_off_force": min(forces), "last_contact_depth": float(ds[last_contact]),
+                   "preload_force": forces[0], "preload_contact_count": counts[0]},
+        "roofline": {"kernel": f"pass {names[dom]}", "bound": "hbm", "achieved": achieved,
+                     "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                     "avg_ms": {k: v for k, v in zip(names, avg_ms)}, "timed_launches": pass_n,
+                     "bytes_per_launch": bytes_dom},
+        "clocks": clocks,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 8 * N * N + 8 * len(ds),
+                "d2h_bytes_per_step": 8 * N * N + 56 * len(ds)},
+        "gpu_launches": int(launches),
+    }
+    if line_note:
+        line["note"] = line_note
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        it, el, _ = cpu_oracle_sample_cached(3)
+        line["cpu_baseline"] = {"value": it / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "3 Polonsky-Keer CG iterations of the 2048^2 preload solve "
+                                          "(oracle FFT mode, numpy pocketfft FP64, single thread)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

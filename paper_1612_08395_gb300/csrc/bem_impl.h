@@ -26,12 +26,12 @@ struct Plan {
 struct Scalars {
   double tol;        // stopping tolerance
   double tau, beta, delta, G, G_old, eps, bnorm, pcrit;
-  double sum_p, sum_dp, n_ol, n_ic, str;
-  int max_iter, iter, done, status, have_tau, pad0;
+  double sum_p, sum_dp, n_ol, n_ic, str, eps_min;
+  int max_iter, iter, done, status, have_tau, it_min;
   unsigned int cnt_a, cnt_c, cnt_e, cnt_r;  // last-block arrival counters
 };
 
-enum { SC_OK = 0, SC_NOCONV = 1, SC_NUMERIC = 2 };
+enum { SC_OK = 0, SC_NOCONV = 1, SC_NUMERIC = 2, SC_STALL = 3 };
 
 // Pass A (row real-to-complex FFT) prologue modes.
 enum PassAMode {
@@ -101,9 +101,10 @@ template <typename T> void launch_convert_out(const T* src, double* dst, size_t 
 template <typename T> void launch_offset(const double* h64, double d, T* c, size_t n, cudaStream_t s);
 template <typename T> void launch_set_from_p(const T* p, uint8_t* S, size_t n, cudaStream_t s);
 template <typename T> void launch_mask_field(T* x, const uint8_t* S, size_t n, cudaStream_t s);
-void launch_refine_apply(double* p64, const float* dp, const uint8_t* S, int project, size_t n,
-                         cudaStream_t s);
+void launch_refine_apply(double* p64, const float* dp, double dscale, const uint8_t* S, int project,
+                         size_t n, cudaStream_t s);
 void launch_to_f32(const double* src, float* dst, size_t n, cudaStream_t s);
+void launch_to_f32_scaled(const double* src, double scale, float* dst, size_t n, cudaStream_t s);
 // S = (p > 0) or (g < 0): active set of the refinement sweep.
 void launch_active_set(const double* p, const double* g, uint8_t* S, size_t n, cudaStream_t s);
 

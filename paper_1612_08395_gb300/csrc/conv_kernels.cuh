@@ -24,6 +24,9 @@ namespace bem {
 
 template <typename T> __device__ __forceinline__ T tabs(T x) { return x < (T)0 ? -x : x; }
 
+// Iterations without halving the best eps before a CG solve is declared stalled.
+constexpr int kStall = 200;
+
 // Sum per-CTA partials in a fixed order (deterministic); result in thread 0.
 template <int NQ>
 __device__ __forceinline__ void sum_partials(const double* part, int n, double (&v)[NQ], double* red) {
@@ -356,6 +359,11 @@ __global__ void __launch_bounds__(1024) k_pass_c(PassArgs<T> a) {
       if (!isfinite(eps) || !isfinite(G)) { sc->status = SC_NUMERIC; done = 1; }
       else if (eps < sc->tol) done = 1;
       else if (sc->iter >= sc->max_iter) { sc->status = SC_NOCONV; done = 1; }
+      // rounding floor: no new minimum of eps for kStall iterations ends the solve
+      if (!done) {
+        if (sc->iter == 1 || eps < 0.5 * sc->eps_min) { sc->eps_min = eps; sc->it_min = sc->iter; }
+        else if (sc->iter - sc->it_min > kStall) { sc->status = SC_STALL; done = 1; }
+      }
     }
     sc->n_ic = nic;
     sc->G = G;
@@ -568,23 +576,29 @@ void launch_pass_c(const PassArgs<T>& a, int mode, cudaStream_t s) {
   }
 }
 
+// Opt every pass kernel into `bytes` of dynamic shared memory (the static
+// reduction scratch counts against the same 227 KB per block, so the request
+// is sized to what the plans need).  Returns the first failure.
 template <typename T>
-void set_smem_attrs() {
-  const int mx = 227 * 1024;
-  cudaFuncSetAttribute(k_pass_a<T, A_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_pass_a<T, A_PK_P>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_pass_a<T, A_PK_T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_pass_a<T, A_CG_T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  if constexpr (sizeof(T) == 8)
-    cudaFuncSetAttribute(k_pass_a<T, A_TORUS>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_pass_b<T, B_CONV>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_pass_b<T, B_SPECTRUM>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_pass_c<T, C_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_pass_c<T, C_PK_G>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_pass_c<T, C_PK_R>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_pass_c<T, C_CG_R>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_pass_c<T, C_CG_G>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_pass_c<T, C_GAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+cudaError_t set_smem_attrs(int bytes) {
+  const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaSuccess, r;
+#define BEM_ATTR(fn) if ((r = cudaFuncSetAttribute(fn, at, bytes)) != cudaSuccess && e == cudaSuccess) e = r
+  BEM_ATTR((k_pass_a<T, A_PLAIN>));
+  BEM_ATTR((k_pass_a<T, A_PK_P>));
+  BEM_ATTR((k_pass_a<T, A_PK_T>));
+  BEM_ATTR((k_pass_a<T, A_CG_T>));
+  if constexpr (sizeof(T) == 8) BEM_ATTR((k_pass_a<T, A_TORUS>));
+  BEM_ATTR((k_pass_b<T, B_CONV>));
+  BEM_ATTR((k_pass_b<T, B_SPECTRUM>));
+  BEM_ATTR((k_pass_c<T, C_PLAIN>));
+  BEM_ATTR((k_pass_c<T, C_PK_G>));
+  BEM_ATTR((k_pass_c<T, C_PK_R>));
+  BEM_ATTR((k_pass_c<T, C_CG_R>));
+  BEM_ATTR((k_pass_c<T, C_CG_G>));
+  BEM_ATTR((k_pass_c<T, C_GAP>));
+#undef BEM_ATTR
+  return e;
 }
 
 static inline int ew_grid(size_t n) {

@@ -3,5 +3,5 @@
 
 namespace bem {
 BEM_INSTANTIATE(float)
-template void set_smem_attrs<float>();
+template cudaError_t set_smem_attrs<float>(int);
 }  // namespace bem

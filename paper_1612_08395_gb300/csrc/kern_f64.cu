@@ -4,20 +4,29 @@
 
 namespace bem {
 BEM_INSTANTIATE(double)
-template void set_smem_attrs<double>();
+template cudaError_t set_smem_attrs<double>(int);
 
-// p64 += dp on S (FP32 correction), optionally projected onto p >= 0.
-__global__ void k_refine_apply(double* p64, const float* dp, const uint8_t* S, int project, size_t n) {
+// p64 += dscale * dp on S (FP32 correction), optionally projected onto p >= 0.
+__global__ void k_refine_apply(double* p64, const float* dp, double dscale, const uint8_t* S,
+                               int project, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     if (!S[i]) continue;
-    double v = p64[i] + (double)dp[i];
+    double v = p64[i] + dscale * (double)dp[i];
     if (project && v < 0.0) v = 0.0;
     p64[i] = v;
   }
 }
-void launch_refine_apply(double* p64, const float* dp, const uint8_t* S, int project, size_t n,
-                         cudaStream_t s) {
-  k_refine_apply<<<ew_grid(n), 256, 0, s>>>(p64, dp, S, project, n);
+void launch_refine_apply(double* p64, const float* dp, double dscale, const uint8_t* S, int project,
+                         size_t n, cudaStream_t s) {
+  k_refine_apply<<<ew_grid(n), 256, 0, s>>>(p64, dp, dscale, S, project, n);
+}
+
+__global__ void k_to_f32_scaled(const double* src, double scale, float* dst, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = (float)(scale * src[i]);
+}
+void launch_to_f32_scaled(const double* src, double scale, float* dst, size_t n, cudaStream_t s) {
+  k_to_f32_scaled<<<ew_grid(n), 256, 0, s>>>(src, scale, dst, n);
 }
 
 __global__ void k_to_f32(const double* src, float* dst, size_t n) {

@@ -13,7 +13,7 @@
 #include "bem_impl.h"
 
 namespace bem {
-template <typename T> void set_smem_attrs();
+template <typename T> cudaError_t set_smem_attrs(int bytes);
 }
 
 using namespace bem;
@@ -235,30 +235,52 @@ void conv_plain(bem_ctx* h, const T* x, T* dst, cudaStream_t s) {
   h->launches += 3;
 }
 
+#define CAPTURE_CHECK(what)                                                                  \
+  do {                                                                                       \
+    cudaError_t le_ = cudaPeekAtLastError();                                                 \
+    if (le_ != cudaSuccess) {                                                                \
+      cudaGraph_t g_;                                                                        \
+      cudaStreamEndCapture(h->stream, &g_);                                                  \
+      if (g_) cudaGraphDestroy(g_);                                                          \
+      cudaGetLastError();                                                                    \
+      return fail(BEM_ECUDA, "capture: %s failed: %s", what, cudaGetErrorString(le_));      \
+    }                                                                                        \
+  } while (0)
+
 template <typename T>
 int capture(bem_ctx* h, bool pk, bool timed, cudaGraphExec_t* out) {
   cudaGraph_t graph;
   cudaEvent_t* ev = h->ev[pk ? 0 : 1];
   if (timed && !ev[0])
     for (int i = 0; i < 4; ++i) CK(cudaEventCreate(&ev[i]));
+  CK(cudaGetLastError());
   CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
   PassArgs<T> a = make_args<T>(h);
   Fields<T> f = a.f;
   for (int it = 0; it < kChunk; ++it) {
     const bool mark = timed && it == 0;
-    if (mark) cudaEventRecord(ev[0], h->stream);
+    if (mark) cudaEventRecordWithFlags(ev[0], h->stream, cudaEventRecordExternal);
+    CAPTURE_CHECK("event 0");
     launch_pass_a<T>(a, pk ? A_PK_P : A_CG_T, h->stream);
-    if (mark) cudaEventRecord(ev[1], h->stream);
+    CAPTURE_CHECK("pass A");
+    if (mark) cudaEventRecordWithFlags(ev[1], h->stream, cudaEventRecordExternal);
     launch_pass_b<T>(a, B_CONV, h->stream);
-    if (mark) cudaEventRecord(ev[2], h->stream);
+    CAPTURE_CHECK("pass B");
+    if (mark) cudaEventRecordWithFlags(ev[2], h->stream, cudaEventRecordExternal);
     launch_pass_c<T>(a, pk ? C_PK_G : C_CG_R, h->stream);
-    if (mark) cudaEventRecord(ev[3], h->stream);
+    CAPTURE_CHECK("pass C");
+    if (mark) cudaEventRecordWithFlags(ev[3], h->stream, cudaEventRecordExternal);
+    CAPTURE_CHECK("event 3");
     if (pk) {
       launch_pass_a<T>(a, A_PK_T, h->stream);
+      CAPTURE_CHECK("pass A (t)");
       launch_pass_b<T>(a, B_CONV, h->stream);
+      CAPTURE_CHECK("pass B (t)");
       launch_pass_c<T>(a, C_PK_R, h->stream);
+      CAPTURE_CHECK("pass C (t)");
     } else {
       launch_cg_update<T>(a.pl, f, h->partE, h->sc, h->ew_ngrid, h->stream);
+      CAPTURE_CHECK("cg update");
     }
   }
   cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
@@ -297,6 +319,8 @@ struct StepOut {
   int status = BEM_OK;
 };
 
+// SC_STALL (eps stopped falling: the arithmetic's rounding floor) counts as
+// converged; final_eps reports where it stopped.
 int map_status(int sc_status) {
   if (sc_status == SC_NOCONV) return BEM_ENOCONV;
   if (sc_status == SC_NUMERIC) return BEM_ENUMERIC;
@@ -414,15 +438,17 @@ int refine(bem_ctx* h, double d, bool adhesive, int sweeps, double tol64, StepOu
     double res = 0, scale = 0;
     CKR(max_abs_on_set(h, h->f64.g, &res));
     CKR(max_abs_on_set(h, h->f64.c, &scale));
-    if (res <= tol64 * scale) break;
-    launch_to_f32(h->f64.g, h->f32.c, n, h->stream);
+    if (res <= tol64 * scale || !(res > 0)) break;
+    // the FP32 correction solves for dp / res so its data are O(1) in FP32
+    launch_to_f32_scaled(h->f64.g, 1.0 / res, h->f32.c, n, h->stream);
     h->launches += 1;
     CK(cudaMemsetAsync(h->f32.p, 0, n * sizeof(float), h->stream));
     CK(cudaMemsetAsync(h->f32.t, 0, n * sizeof(float), h->stream));
     StepOut cg;
     CKR(run_fixed_cg<float>(h, 1e-6, 2000, 0.0, &cg));
     so->iterations += cg.iterations;
-    launch_refine_apply(h->io64, h->f32.p, h->S, adhesive ? 0 : 1, n, h->stream);
+    if (h->sc_host->status == SC_NUMERIC) { so->status = BEM_ENUMERIC; break; }
+    launch_refine_apply(h->io64, h->f32.p, res, h->S, adhesive ? 0 : 1, n, h->stream);
     h->launches += 1;
   }
   return BEM_OK;
@@ -460,8 +486,12 @@ extern "C" int bem_create(int Nx, int Ny, double dx, double dy, double k, double
     return cleanup(fail(BEM_ECUDA, "stream creation failed"));
   static bool attrs_done = false;
   if (!attrs_done) {
-    set_smem_attrs<float>();
-    set_smem_attrs<double>();
+    // plans never ask for more than 128 KB + one row of dynamic shared memory
+    const int smem_max = 136 * 1024;
+    cudaError_t ea = set_smem_attrs<float>(smem_max);
+    if (ea == cudaSuccess) ea = set_smem_attrs<double>(smem_max);
+    if (ea != cudaSuccess)
+      return cleanup(fail(BEM_ECUDA, "shared-memory opt-in failed: %s", cudaGetErrorString(ea)));
     if (influence_init_nodes() != 0) return cleanup(fail(BEM_ECUDA, "quadrature nodes upload failed"));
     attrs_done = true;
   }
