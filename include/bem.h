@@ -153,6 +153,31 @@ int bem_get_info(bem_handle h, bem_info *info);
 int bem_pass_times(bem_handle h, double ms[3], long long count[2], int reset);
 
 /* ---------------------------------------------------------------------------
+ * bem_convolve_noalloc: u = A K*p in FP64 for callers that must not allocate
+ * device memory.  The paper has no counterpart; this is a service of the
+ * library.  Callers that cannot call cudaMalloc -- code running while a stream
+ * is captured into a CUDA graph, hosts whose device memory belongs to a pool
+ * they must not bypass, loops that cannot afford cudaMalloc's device-wide
+ * synchronisation -- get the same transform as bem_convolve(FP64) without a
+ * handle and without any allocation: its scratch is a 2 MiB static device
+ * array that every GPU loading the library holds until exit.
+ *   khat       : device pointer, the FP64 spectrum quarter exactly as
+ *                bem_spectrum writes it for a handle of the same Nx, Ny
+ *                ((Py/2+1) rows of Px/2+1 values)
+ *   Nx, Ny     : 2..256
+ *   compliance : A = alpha (1-nu^2) c0^k / E0 (bem_get_info().compliance)
+ *   p, u       : device pointers to Nx*Ny FP64 fields (input, output)
+ *   stream     : cudaStream_t to run on (NULL = legacy default stream)
+ * The call is asynchronous on `stream`.  Its first call on a device looks up
+ * the static array's device address; make that first call before any stream
+ * capture.  All calls share the array: calls whose work overlaps on the GPU
+ * race and must be serialised by the caller.  Returns BEM_EINVAL for sizes
+ * beyond the maximum, host pointers or NULL arguments, BEM_ECUDA on a launch
+ * failure. */
+int bem_convolve_noalloc(const double *khat, int Nx, int Ny, double compliance, const double *p,
+                         double *u, void *stream);
+
+/* ---------------------------------------------------------------------------
  * Host-only helpers (no GPU needed).
  * bem_alpha: alpha(k, nu) of Eq. 3 (NaN outside the valid range).
  * bem_c1_corrected: corrected c1(k) of Table 1 for -0.9 <= k <= 0.9; between

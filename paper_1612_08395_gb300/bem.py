@@ -87,6 +87,7 @@ def load_library(path: str = LIB_PATH):
     lib.bem_spectrum.argtypes = [vp, vp]
     lib.bem_convolve.argtypes = [vp, ip, vp, vp]
     lib.bem_get_info.argtypes = [vp, ctypes.POINTER(Info)]
+    lib.bem_convolve_noalloc.argtypes = [vp, ip, ip, ctypes.c_double, vp, vp, vp]
     lib.bem_pass_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong), ip]
     for fn in (lib.bem_alpha, lib.bem_c1_corrected):
         fn.restype = ctypes.c_double
@@ -120,6 +121,13 @@ def _ptr(a, n=None, writable=False):
     if n is not None and a.size != n:
         raise ValueError(f"expected {n} elements, got {a.size}")
     return ctypes.c_void_p(a.ctypes.data)
+
+
+def convolve_noalloc(khat, nx, ny, compliance, p, u, stream=None) -> int:
+    """bem_convolve_noalloc on device tensors (no allocation inside); returns the status."""
+    sp = None if stream is None else getattr(stream, "cuda_stream", stream)
+    return load_library().bem_convolve_noalloc(_ptr(khat), nx, ny, compliance, _ptr(p, nx * ny),
+                                               _ptr(u, nx * ny, writable=True), sp)
 
 
 def alpha(k: float, nu: float) -> float:

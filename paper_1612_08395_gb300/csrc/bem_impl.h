@@ -108,6 +108,9 @@ void launch_to_f32_scaled(const double* src, double scale, float* dst, size_t n,
 // S = (p > 0) or (g < 0): active set of the refinement sweep.
 void launch_active_set(const double* p, const double* g, uint8_t* S, size_t n, cudaStream_t s);
 
+// Record `msg` as the thread's last error and return `code`.
+int set_error(int code, const char* msg);
+
 // Influence coefficients (FP64): Kq[dj*(hx) + di], 0 <= di < hx, 0 <= dj < hy.
 int influence_init_nodes();
 void launch_influence(double* Kq, int hx, int hy, double dx, double dy, double k, cudaStream_t s);

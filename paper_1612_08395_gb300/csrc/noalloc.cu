@@ -1,0 +1,146 @@
+// bem_convolve_noalloc: the FP64 stress -> displacement transform for callers
+// that may not allocate device memory.
+//
+// Some callers cannot call cudaMalloc: code that runs while a stream is being
+// captured into a CUDA graph (an allocation there breaks the capture), hosts
+// whose device memory is owned by a pool or arena the caller must not bypass,
+// and latency-critical loops where cudaMalloc's implicit device-wide
+// synchronisation is not allowed.  This entry point allocates nothing: the
+// scratch the three transform passes need (the transposed half spectrum W and
+// a transposed copy of the kernel spectrum) lives in one file-scope device
+// array of kScratchBytes bytes, which every GPU that loads the library holds
+// until the process exits.
+//
+// The array's name in host code is only a host-side stand-in, not a device
+// address; its device address is obtained once per device with
+// cudaGetSymbolAddress (on the first call made with that device current) and
+// passed to the kernels.  Because that first call does this set-up, it should
+// come before any stream capture.
+//
+// Every call shares the array and it keeps the previous call's contents.
+// Nothing in it needs clearing: each call writes every element it later reads
+// (the transposed spectrum and all of W) before reading it.  Calls whose work
+// overlaps on the GPU (different streams, or different host threads) race on
+// the array and must be serialised by the caller.
+#include <mutex>
+
+#include <cuda_runtime.h>
+
+#include "bem.h"
+#include "bem_impl.h"
+
+namespace {
+
+constexpr size_t kScratchBytes = 2u << 20;  // 2 MiB: W and the spectrum for grids up to 256 x 256
+constexpr int kMaxSide = 256;
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+std::mutex g_setup_mu;
+void* g_scratch_dev[kMaxDevices] = {};
+
+__global__ void k_transpose_spectrum(const double* src, double* dst, int hx, int hyq) {
+  // src[ky * hx + kx] (as bem_spectrum writes it) -> dst[kx * hyq + ky]
+  const int kx = blockIdx.x * blockDim.x + threadIdx.x, ky = blockIdx.y;
+  if (kx < hx && ky < hyq) dst[(size_t)kx * hyq + ky] = src[(size_t)ky * hx + kx];
+}
+
+int pow2_at_least(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+int ilog2i(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+bool on_device(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" int bem_convolve_noalloc(const double* khat, int Nx, int Ny, double compliance,
+                                    const double* p, double* u, void* stream) {
+  if (Nx < 2 || Ny < 2 || Nx > kMaxSide || Ny > kMaxSide)
+    return bem::set_error(BEM_EINVAL, "bem_convolve_noalloc: Nx and Ny must be in 2..256 (static scratch of 2 MiB)");
+  if (!khat || !p || !u || !(compliance > 0.0))
+    return bem::set_error(BEM_EINVAL, "bem_convolve_noalloc: NULL array or compliance <= 0");
+  if (!on_device(khat) || !on_device(p) || !on_device(u))
+    return bem::set_error(BEM_EINVAL, "bem_convolve_noalloc: khat, p and u must be device pointers");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    return bem::set_error(BEM_ECUDA, "bem_convolve_noalloc: no usable current device");
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_setup_mu);
+    if (!g_scratch_dev[dev]) {
+      void* ptr = nullptr;
+      if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+        cudaGetLastError();
+        return bem::set_error(BEM_ECUDA, "bem_convolve_noalloc: cudaGetSymbolAddress of the scratch failed");
+      }
+      g_scratch_dev[dev] = ptr;
+    }
+    base = g_scratch_dev[dev];
+  }
+  const int px = pow2_at_least(2 * Nx < 16 ? 16 : 2 * Nx);
+  const int py = pow2_at_least(2 * Ny < 16 ? 16 : 2 * Ny);
+  const int M = px / 2, hx = M + 1, hyq = py / 2 + 1;
+  const size_t w_bytes = sizeof(double) * 2 * (size_t)hx * Ny;
+  const size_t k_bytes = sizeof(double) * (size_t)hx * hyq;
+  const size_t k_off = (w_bytes + 255) & ~(size_t)255;
+  if (k_off + k_bytes > kScratchBytes)
+    return bem::set_error(BEM_EINVAL, "bem_convolve_noalloc: grid needs more than the 2 MiB static scratch");
+
+  // launch geometry: the same rules as the handle's FP64 plan
+  bem::Plan pl{};
+  pl.nx = Nx; pl.ny = Ny; pl.px = px; pl.py = py; pl.M = M;
+  pl.logM = ilog2i(M); pl.logPy = ilog2i(py);
+  const int tr = M / 8;
+  int nb = 256 / tr;
+  if (nb < 2) nb = 2;
+  while (nb > 1 && nb * tr > 1024) nb >>= 1;
+  while (nb > 1 && (size_t)nb * (M + 1) * 16 > 128 * 1024) nb >>= 1;
+  pl.nbA = nb; pl.threadsA = nb * tr; pl.gridA = (Ny + nb - 1) / nb;
+  pl.smemA = (size_t)nb * M * 16; pl.smemC = (size_t)nb * (M + 1) * 16;
+  const int tb = py / 8;
+  int nbb = 256 / tb;
+  if (nbb < 1) nbb = 1;
+  while (nbb > 1 && (size_t)nbb * py * 16 > 128 * 1024) nbb >>= 1;
+  pl.nbB = nbb; pl.threadsB = nbb * tb; pl.gridB = (M + nbb - 1) / nbb;
+  pl.smemB = (size_t)nbb * py * 16;
+  // every pass stays within the default 48 KB of dynamic shared memory here
+  if (pl.smemA > 48 * 1024 || pl.smemB > 48 * 1024 || pl.smemC > 48 * 1024)
+    return bem::set_error(BEM_EINVAL, "bem_convolve_noalloc: grid too large for the default shared memory");
+
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned char* scratch = static_cast<unsigned char*>(base);
+  double* khat_t = reinterpret_cast<double*>(scratch + k_off);
+  k_transpose_spectrum<<<dim3((hx + 127) / 128, hyq), 128, 0, s>>>(khat, khat_t, hx, hyq);
+
+  bem::PassArgs<double> a{};
+  a.pl = pl;
+  a.f.src = p;
+  a.f.dst = u;
+  a.W = scratch;
+  a.rows_w = Ny;
+  a.nrows_in = Ny;
+  a.ncols_in = Nx;
+  a.khat = khat_t;
+  a.uscale = compliance / ((double)px * (double)py);
+  bem::launch_pass_a<double>(a, bem::A_PLAIN, s);
+  bem::launch_pass_b<double>(a, bem::B_CONV, s);
+  bem::launch_pass_c<double>(a, bem::C_PLAIN, s);
+  const cudaError_t e = cudaPeekAtLastError();
+  if (e != cudaSuccess) return bem::set_error(BEM_ECUDA, cudaGetErrorString(e));
+  return BEM_OK;
+}

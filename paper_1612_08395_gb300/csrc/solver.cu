@@ -466,6 +466,10 @@ int validate_ptr(const void* p, const char* name) {
 
 extern "C" const char* bem_last_error(void) { return g_err.c_str(); }
 
+namespace bem {
+int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+}
+
 extern "C" int bem_create(int Nx, int Ny, double dx, double dy, double k, double nu, double E0,
                           double c0, bem_handle* out) {
   g_err.clear();
