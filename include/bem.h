@@ -75,7 +75,7 @@ typedef struct {
  * bem_create: validate, compute A (Eqs. 2-4, 12), tabulate the influence
  * coefficients K(di, dj) of Eq. 9 for 0 <= di <= Px/2, 0 <= dj <= Py/2 in FP64
  * on the device, wrap them evenly onto the Px x Py torus (Px, Py = powers of two
- * >= 2 Nx, 2 Ny, at least 16), and take its spectrum (Eq. 13: FFT(K)), kept as
+ * >= 2 Nx, 2 Ny, at least 32), and take its spectrum (Eq. 13: FFT(K)), kept as
  * the real quarter in FP64 and FP32.
  *   Nx, Ny : 2..4096;  dx, dy > 0;  -1 < k < 1;  -1 < nu <= 0.5 with
  *   beta(k,nu)^2 > 0 (Eq. 4);  E0 > 0;  c0 > 0;  out != NULL.

@@ -6,18 +6,36 @@
 
 namespace bem {
 
+// One FFT length of the plan: 2^logL points, first DIF stage radix 2^r0
+// (r0 = logL mod 3; 0 means radix 8), shared-memory swizzle and the row
+// stride (in elements) of each transform's region in shared memory.
+struct Geo {
+  int logL, r0;
+  int sa, sb, sc, sd;
+  int rs;
+};
+
+// Per-length index tables on the device (int32):
+//   so[ls * 8 + r] = swz(r << ls), ls = 0..13     (112 entries)
+//   sp[k]          = swz(dig_pos(k)), k < 2^logL  (digit-reversed, swizzled)
+constexpr int kSoEntries = 112;
+void launch_geo_tables(int* so, int* sp, Geo g, int esize, cudaStream_t s);
+
 // Launch geometry of the three convolution passes for one handle.
-//   rows  : field rows (Ny), cols: field columns (Nx)
-//   Px,Py : torus sides (powers of two >= 2 Nx, 2 Ny, >= 16); M = Px/2
-//   W     : intermediate spectrum, (M+1) rows (kx = 0..M) of `rows` complex
-//           values: row kx holds column kx of the row transforms (transposed
-//           so the column pass reads contiguous memory).
+//   ny, nx: field rows and columns;  Px, Py: torus sides (powers of two
+//   >= 2 Nx, 2 Ny, at least 32);  M = Px/2 (complex row-FFT length).
+//   W: intermediate spectrum, M+1 rows (kx = 0..M) of `ny` complex values --
+//   row kx holds column kx of the row transforms, so the column pass reads
+//   contiguous memory.
 struct Plan {
-  int nx, ny, px, py, M, logM, logPy;
-  int nbA;    // field rows per CTA in passes A and C
+  int nx, ny, px, py, M;
+  Geo gA;     // length M: row transforms of passes A and C
+  Geo gB;     // length Py: column transforms of pass B
+  int nbA;    // field rows per CTA in passes A and C (power of two)
+  int lognbA;
   int nbB;    // spectrum columns per CTA in pass B
   int gridA;  // = ceil(ny / nbA)
-  int gridB;  // = ceil(M / nbB)   (column 0 CTA also carries column M)
+  int gridB;  // = ceil((M + 1) / nbB)
   int threadsA, threadsB;
   size_t smemA, smemB, smemC;
 };
@@ -74,6 +92,13 @@ struct PassArgs {
   int ncols_in;         // columns fed to pass A (= nx, or Px for the torus)
   const double* kq64;   // A_TORUS: influence quarter, (Py/2+1) x (M+1)
   const T* khat;        // B_CONV: spectrum quarter, transposed: [kx][ky], ky <= Py/2
+  const void* twA;      // stage twiddle tables, length M (C<T>)
+  const void* twB;      // stage twiddle tables, length Py (C<T>)
+  const void* twS;      // exp(-i pi k / M), k = 0..M (C<T>): real-FFT split
+  const int* soA;       // index tables of length M and Py (see Geo)
+  const int* spA;
+  const int* soB;
+  const int* spB;
   double* khat64_out;   // B_SPECTRUM outputs ([kx][ky])
   float* khat32_out;
   double uscale;        // pass C: A / (Px Py)
@@ -110,6 +135,14 @@ void launch_active_set(const double* p, const double* g, uint8_t* S, size_t n, c
 
 // Record `msg` as the thread's last error and return `code`.
 int set_error(int code, const char* msg);
+
+// Twiddle tables of one FFT length (stage tables, 2^logL entries reserved) and
+// of the real-FFT split (M+1 entries), FP64 and FP32 copies.
+void launch_twiddles(double2* t64, float2* t32, int logL, cudaStream_t s);
+void launch_split_twiddles(double2* t64, float2* t32, int M, cudaStream_t s);
+// Geometry (swizzle, first-stage radix, row stride) of a length-2^logL
+// transform with `rows` transforms per CTA, for elements of esize bytes.
+Geo make_geo(int logL, int rows, int esize);
 
 // Influence coefficients (FP64): Kq[dj*(hx) + di], 0 <= di < hx, 0 <= dj < hy.
 int influence_init_nodes();

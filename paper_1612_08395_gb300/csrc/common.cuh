@@ -1,5 +1,5 @@
-// Shared device helpers: complex arithmetic, shared-memory Stockham FFT,
-// FP64 block reductions.  sm_103a only.
+// Shared device helpers: complex arithmetic, in-place radix-8 FFT stages in
+// shared memory, FP64 block reductions.  sm_103a only.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -23,10 +23,6 @@ template <typename T> __device__ __forceinline__ C<T> scale(C<T> a, T s) { retur
 template <typename T, int S> __device__ __forceinline__ C<T> mul_si(C<T> a) {
   return S > 0 ? mk<T>(-a.y, a.x) : mk<T>(a.y, -a.x);
 }
-
-// exp(i*pi*x)
-__device__ __forceinline__ float2 expipi(float x) { float s, c; sincospif(x, &s, &c); return make_float2(c, s); }
-__device__ __forceinline__ double2 expipi(double x) { double s, c; sincospi(x, &s, &c); return make_double2(c, s); }
 
 template <typename T> struct consts;
 template <> struct consts<float> { static constexpr float rsqrt2 = 0.70710678118654752440f; };
@@ -59,80 +55,120 @@ template <typename T, int S> __device__ __forceinline__ void dft8(C<T>* v) {
 }
 
 // ---------------------------------------------------------------------------
-// Stockham autosort FFT in shared memory, in place (values go through
-// registers between two barriers).  One sequence of length L = 2^logL
-// (logL >= 3) at `s`; the calling thread is butterfly lane j0 in [0, L/8) of
-// that sequence; every thread of the block must call it (it synchronises).
-// Each pass moves 8 elements per thread: radix 8, or on the first pass a
-// radix-4 (x2) or radix-2 (x4) step when logL is not a multiple of 3.
-// Twiddle factors: exp(S*2*pi*i*r*k/(Ns*R)) from one sincospi per butterfly
-// and its powers.  Unnormalised in both directions.
-template <typename T, int S>
-__device__ __forceinline__ void twiddle8(C<T>* v, int k, int NsR) {
-  C<T> w1 = expipi((T)(S * 2) * (T)k / (T)NsR);
-  C<T> w2 = mul<T>(w1, w1);
-  C<T> w3 = mul<T>(w2, w1);
-  C<T> w4 = mul<T>(w2, w2);
-  v[1] = mul<T>(v[1], w1);
-  v[2] = mul<T>(v[2], w2);
-  v[3] = mul<T>(v[3], w3);
-  v[4] = mul<T>(v[4], w4);
-  v[5] = mul<T>(v[5], mul<T>(w4, w1));
-  v[6] = mul<T>(v[6], mul<T>(w3, w3));
-  v[7] = mul<T>(v[7], mul<T>(w4, w3));
+// In-place radix-8 FFT stages in shared memory.
+//
+// A length L = 2^m transform runs as a decimation-in-frequency (DIF) sequence
+// of stages: first one stage of radix R0 = 2^(m mod 3) (if m is not a multiple
+// of 3) with stride L/R0, then radix-8 stages with strides ..., 64, 8, 1.  A
+// stage of radix R and stride s combines, for butterfly offset o < s in
+// group g, the elements g*R*s + o + r*s (r < R) -- each thread reads and
+// writes the same R positions, so one barrier between stages suffices.  DIF
+// leaves the spectrum in digit-reversed order: frequency k sits at position
+// dig_pos(k).  The inverse runs the same stages in the opposite order as
+// decimation-in-time (DIT) with conjugate twiddles, taking digit-reversed
+// input back to natural order.  Twiddles come from per-stage tables:
+// entry o of the stage (R, s) table is exp(-2 pi i o / (R s)); a butterfly
+// reads its base twiddle once and forms the powers it needs.
+//
+// Shared-memory positions go through an XOR swizzle of the low bank bits
+// (4 bits for 8-byte elements, 3 bits for 16-byte ones) chosen per length so
+// that every stage's accesses, and the digit-reversed reads, avoid bank
+// conflicts.
+struct Swz {
+  int a, b, c, d;
+};
+template <typename T> __device__ __forceinline__ int swz(int i, const Swz& z);
+template <> __device__ __forceinline__ int swz<float>(int i, const Swz& z) {
+  return i ^ ((((i >> z.a) ^ (i >> z.b)) & 7) | ((((i >> z.c) ^ (i >> z.d)) & 1) << 3));
+}
+template <> __device__ __forceinline__ int swz<double>(int i, const Swz& z) {
+  return i ^ ((((i >> z.a) ^ (i >> z.b)) & 3) | ((((i >> z.c) ^ (i >> z.d)) & 1) << 2));
 }
 
-template <typename T, int S>
-__device__ void fft_smem(C<T>* s, int logL, int j0) {
-  const int L = 1 << logL;
-  const int L8 = L >> 3;
-  int logNs = 0;
-  const int rem = logL % 3;
+// Position of frequency k after the DIF stages of a length-2^logL transform.
+__host__ __device__ __forceinline__ int dig_pos(int k, int logL, int r0) {
+  int p = 0, sh = logL;
+  if (r0) {
+    sh -= r0;
+    p = (k & ((1 << r0) - 1)) << sh;
+    k >>= r0;
+  }
+  while (sh > 0) {
+    sh -= 3;
+    p |= (k & 7) << sh;
+    k >>= 3;
+  }
+  return p;
+}
+
+// Offset of the twiddle table of the radix-8 stage with stride 2^ls.
+__host__ __device__ __forceinline__ int tw_off8(int logL, int r0, int ls) {
+  const int top = 1 << (logL - r0);
+  return (r0 ? top : 0) + (top - (8 << ls)) / 7;
+}
+
+template <typename T>
+__device__ __forceinline__ void powers8(C<T> w, C<T>* wp) {
+  wp[1] = w;
+  wp[2] = mul<T>(w, w);
+  wp[3] = mul<T>(wp[2], w);
+  wp[4] = mul<T>(wp[2], wp[2]);
+  wp[5] = mul<T>(wp[4], w);
+  wp[6] = mul<T>(wp[3], wp[3]);
+  wp[7] = mul<T>(wp[4], wp[3]);
+}
+
+// The swizzle is linear over GF(2) (XOR of shifted, masked bits), and within
+// a stage the group base and the r * stride term occupy disjoint bits, so
+// swz(base + r s) = swz(base) ^ swz(r s).  The eight values swz(r << ls) of
+// every stride are precomputed per transform length (table `so`, 8 entries
+// per ls = 0..13), leaving one XOR per shared-memory access.
+
+// DIF radix-8 stage with stride 2^ls; thread = butterfly t (t < L/8);
+// tw = this stage's twiddle table; so8 = swz(r << ls), r = 0..7.
+template <typename T>
+__device__ __forceinline__ void dif8(C<T>* buf, int t, int ls, const C<T>* tw, const Swz& z,
+                                     const int* so8) {
+  const int o = t & ((1 << ls) - 1);
+  const int sb = swz<T>(((t >> ls) << (ls + 3)) + o, z);
+  const int4 s0 = __ldg(reinterpret_cast<const int4*>(so8));
+  const int4 s1 = __ldg(reinterpret_cast<const int4*>(so8) + 1);
+  const int ix[8] = {sb ^ s0.x, sb ^ s0.y, sb ^ s0.z, sb ^ s0.w, sb ^ s1.x, sb ^ s1.y, sb ^ s1.z, sb ^ s1.w};
   C<T> v[8];
-  if (rem == 1) {  // radix 2, four butterflies, Ns = 1 (no twiddles)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) { int j = j0 + q * L8; v[2 * q] = s[j]; v[2 * q + 1] = s[j + (L >> 1)]; }
-    __syncthreads();
+  for (int r = 0; r < 8; ++r) v[r] = buf[ix[r]];
+  dft8<T, -1>(v);
+  if (ls > 0) {
+    C<T> wp[8];
+    powers8<T>(__ldg(tw + o), wp);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      int j = j0 + q * L8;
-      dft2<T, S>(v[2 * q], v[2 * q + 1]);
-      s[2 * j] = v[2 * q]; s[2 * j + 1] = v[2 * q + 1];
-    }
-    __syncthreads();
-    logNs = 1;
-  } else if (rem == 2) {  // radix 4, two butterflies, Ns = 1
-    const int L4 = L >> 2;
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      int j = j0 + q * L8;
-#pragma unroll
-      for (int r = 0; r < 4; ++r) v[4 * q + r] = s[j + r * L4];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      int j = j0 + q * L8;
-      dft4<T, S>(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-#pragma unroll
-      for (int r = 0; r < 4; ++r) s[4 * j + r] = v[4 * q + r];
-    }
-    __syncthreads();
-    logNs = 2;
+    for (int q = 1; q < 8; ++q) v[q] = mul<T>(v[q], wp[q]);
   }
-  for (; logNs < logL; logNs += 3) {
-    const int Ns = 1 << logNs;
 #pragma unroll
-    for (int r = 0; r < 8; ++r) v[r] = s[j0 + r * L8];
-    __syncthreads();
-    const int k = j0 & (Ns - 1);
-    if (logNs > 0) twiddle8<T, S>(v, k, Ns << 3);
-    dft8<T, S>(v);
-    const int base = ((j0 >> logNs) << (logNs + 3)) + k;
+  for (int q = 0; q < 8; ++q) buf[ix[q]] = v[q];
+}
+
+// DIT radix-8 inverse stage with stride 2^ls (conjugate twiddles before the butterfly).
+template <typename T>
+__device__ __forceinline__ void dit8(C<T>* buf, int t, int ls, const C<T>* tw, const Swz& z,
+                                     const int* so8) {
+  const int o = t & ((1 << ls) - 1);
+  const int sb = swz<T>(((t >> ls) << (ls + 3)) + o, z);
+  const int4 s0 = __ldg(reinterpret_cast<const int4*>(so8));
+  const int4 s1 = __ldg(reinterpret_cast<const int4*>(so8) + 1);
+  const int ix[8] = {sb ^ s0.x, sb ^ s0.y, sb ^ s0.z, sb ^ s0.w, sb ^ s1.x, sb ^ s1.y, sb ^ s1.z, sb ^ s1.w};
+  C<T> v[8];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) s[base + r * Ns] = v[r];
-    __syncthreads();
+  for (int r = 0; r < 8; ++r) v[r] = buf[ix[r]];
+  if (ls > 0) {
+    C<T> wp[8];
+    powers8<T>(conj<T>(__ldg(tw + o)), wp);
+#pragma unroll
+    for (int r = 1; r < 8; ++r) v[r] = mul<T>(v[r], wp[r]);
   }
+  dft8<T, 1>(v);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) buf[ix[q]] = v[q];
 }
 
 // ---------------------------------------------------------------------------

@@ -4,14 +4,23 @@
 //
 //   pass A  rows:    real row of Nx values (zero-padded to Px) -> half
 //                    spectrum X[kx], kx = 0..Px/2, via one complex FFT of
-//                    length Px/2 on (x[2n], x[2n+1]) and the standard split.
-//                    Written transposed: W[kx][iy].
-//   pass B  columns: for each kx, forward FFT of length Py of the Ny values
-//                    (zero-padded), multiply by the real spectrum K^(ky, kx),
-//                    inverse FFT, keep Ny values, in place in W.  Columns 0
-//                    and Px/2 are real and ride together in one complex FFT.
+//                    length M = Px/2 on (x[2n], x[2n+1]) and the standard
+//                    split.  Written transposed: W[kx][iy].
+//   pass B  columns: for each kx, DIF FFT of length Py of the Ny values
+//                    (zero-padded), multiply by the real spectrum K^(ky, kx)
+//                    in digit-reversed order, DIT inverse FFT, keep Ny values,
+//                    in place in W.
 //   pass C  rows:    complex-to-real inverse of length Px from the half
 //                    spectrum, keep Nx values, scale by A/(Px Py), epilogue.
+//
+// The transform length is a template parameter (dispatched at launch), so
+// strides, masks and swizzle constants fold into immediates.  Because
+// Px >= 2 Nx and Py >= 2 Ny, the nonzero inputs of every forward transform
+// fill its first half and only the first half of every inverse is kept: the
+// first forward stage reads just those inputs straight from global memory
+// and the last inverse stage computes and writes just those outputs.
+// Prologue and epilogue field loads are issued together (gather, then
+// compute, then store) so their latencies overlap.
 //
 // Every kernel that belongs to a CG loop returns at once when the solve's
 // `done` flag is set, so a captured chunk of iterations can run past
@@ -19,6 +28,7 @@
 #pragma once
 #include "bem_impl.h"
 #include "common.cuh"
+#include "geo_table.h"
 
 namespace bem {
 
@@ -39,304 +49,536 @@ __device__ __forceinline__ void sum_partials(const double* part, int n, double (
   block_sum<NQ>(v, red);
 }
 
+// Compile-time description of a length-2^LOGL transform for element type T.
+template <typename T, int LOGL>
+struct FftC {
+  static constexpr int L = 1 << LOGL, L8 = L >> 3, R0 = LOGL % 3;
+  static constexpr int LS_TOP = R0 == 0 ? LOGL - 6 : LOGL - R0 - 3;  // largest radix-8 stride below stage 0
+  using G = GeoC<(int)sizeof(T), LOGL>;
+  static __device__ __forceinline__ int sw(int i) {
+    if (sizeof(T) == 4)
+      return i ^ ((((i >> G::a) ^ (i >> G::b)) & 7) | ((((i >> G::c) ^ (i >> G::d)) & 1) << 3));
+    return i ^ ((((i >> G::a) ^ (i >> G::b)) & 3) | ((((i >> G::c) ^ (i >> G::d)) & 1) << 2));
+  }
+  // n of element e (0..7) of thread t in stage 0 (the first DIF stage)
+  static __device__ __forceinline__ int n0(int t, int e) {
+    if (R0 == 0) return t + e * L8;
+    if (R0 == 2) return t + (e >> 2) * L8 + (e & 3) * (L >> 2);
+    return t + (e >> 1) * L8 + (e & 1) * (L >> 1);
+  }
+  // whether element e of stage 0 lies in the first half (t < L8 always)
+  static __device__ __forceinline__ constexpr bool first_half(int e) {
+    return R0 == 0 ? e < 4 : (R0 == 2 ? (e & 3) < 2 : (e & 1) == 0);
+  }
+  // stage 0 butterflies on the 8 values of a thread (DIF: butterfly, then twiddle)
+  static __device__ __forceinline__ void stage0_fwd(C<T>* v, int t, const C<T>* tw) {
+    if (R0 == 0) {
+      dft8<T, -1>(v);
+      C<T> wp[8];
+      powers8<T>(__ldg(tw + t), wp);
+#pragma unroll
+      for (int q = 1; q < 8; ++q) v[q] = mul<T>(v[q], wp[q]);
+    } else if (R0 == 2) {
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        C<T>* u = v + 4 * i;
+        dft4<T, -1>(u[0], u[1], u[2], u[3]);
+        const C<T> w = __ldg(tw + t + i * L8), w2 = mul<T>(w, w), w3 = mul<T>(w2, w);
+        u[1] = mul<T>(u[1], w); u[2] = mul<T>(u[2], w2); u[3] = mul<T>(u[3], w3);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        C<T>* u = v + 2 * i;
+        dft2<T, -1>(u[0], u[1]);
+        u[1] = mul<T>(u[1], __ldg(tw + t + i * L8));
+      }
+    }
+  }
+  // inverse of stage 0 (DIT: conjugate twiddle, then butterfly)
+  static __device__ __forceinline__ void stage0_inv(C<T>* v, int t, const C<T>* tw) {
+    if (R0 == 0) {
+      C<T> wp[8];
+      powers8<T>(conj<T>(__ldg(tw + t)), wp);
+#pragma unroll
+      for (int r = 1; r < 8; ++r) v[r] = mul<T>(v[r], wp[r]);
+      dft8<T, 1>(v);
+    } else if (R0 == 2) {
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        C<T>* u = v + 4 * i;
+        const C<T> w = conj<T>(__ldg(tw + t + i * L8)), w2 = mul<T>(w, w), w3 = mul<T>(w2, w);
+        u[1] = mul<T>(u[1], w); u[2] = mul<T>(u[2], w2); u[3] = mul<T>(u[3], w3);
+        dft4<T, 1>(u[0], u[1], u[2], u[3]);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        C<T>* u = v + 2 * i;
+        u[1] = mul<T>(u[1], conj<T>(__ldg(tw + t + i * L8)));
+        dft2<T, 1>(u[0], u[1]);
+      }
+    }
+  }
+  // shared-memory index of element e of stage 0 for thread t
+  static __device__ __forceinline__ int ix0(int t, int e) { return sw(n0(t, e)); }
+
+  // radix-8 DIF / DIT stage with compile-time stride 2^LS (after unrolling)
+  static __device__ __forceinline__ void dif(C<T>* buf, int t, int ls, const C<T>* tw) {
+    const int o = t & ((1 << ls) - 1);
+    const int sb = sw(((t >> ls) << (ls + 3)) + o);
+    C<T> v[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) v[r] = buf[sb ^ sw(r << ls)];
+    dft8<T, -1>(v);
+    if (ls > 0) {
+      C<T> wp[8];
+      powers8<T>(__ldg(tw + tw_off8(LOGL, R0, ls) + o), wp);
+#pragma unroll
+      for (int q = 1; q < 8; ++q) v[q] = mul<T>(v[q], wp[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) buf[sb ^ sw(q << ls)] = v[q];
+  }
+  static __device__ __forceinline__ void dit(C<T>* buf, int t, int ls, const C<T>* tw) {
+    const int o = t & ((1 << ls) - 1);
+    const int sb = sw(((t >> ls) << (ls + 3)) + o);
+    C<T> v[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) v[r] = buf[sb ^ sw(r << ls)];
+    if (ls > 0) {
+      C<T> wp[8];
+      powers8<T>(conj<T>(__ldg(tw + tw_off8(LOGL, R0, ls) + o)), wp);
+#pragma unroll
+      for (int r = 1; r < 8; ++r) v[r] = mul<T>(v[r], wp[r]);
+    }
+    dft8<T, 1>(v);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) buf[sb ^ sw(q << ls)] = v[q];
+  }
+};
+
 // ---------------------------------------------------------------------------
+// Pass-A prologue, in two phases: gather the fields of one field index, then
+// compute the transform input (with the CG work of the mode) and store.
+template <typename T>
+struct PIn {
+  T p, t, g;
+  uint8_t s;
+};
+
 template <typename T, int MODE>
+__device__ __forceinline__ void pro_gather(const PassArgs<T>& a, size_t i, PIn<T>& x) {
+  if (MODE == A_PLAIN) {
+    x.p = __ldg(a.f.src + i);
+  } else if (MODE == A_PK_P) {
+    x.p = a.f.p[i]; x.t = a.f.t[i]; x.g = a.f.g[i];
+  } else if (MODE == A_PK_T) {
+    x.p = a.f.p[i]; x.t = a.f.t[i]; x.g = a.f.g[i];
+  } else if (MODE == A_CG_T) {
+    x.s = a.f.S[i]; x.t = a.f.t[i]; x.g = a.f.g[i];
+  }
+}
+
+template <typename T, int MODE>
+__device__ __forceinline__ T pro_apply(const PassArgs<T>& a, size_t i, const PIn<T>& x, bool upd,
+                                       T tau, T beta, T* acc) {
+  if (MODE == A_PLAIN) {
+    return x.p;
+  } else if (MODE == A_PK_P) {
+    // Polonsky-Keer steps 7-8: p <- max(p - tau t, 0) on the contact set,
+    // then the overlap step p = -tau g where p = 0 and g < 0.
+    T q = x.p;
+    if (upd) {
+      if (x.p > (T)0) {
+        q = x.p - tau * x.t;
+        q = q > (T)0 ? q : (T)0;
+      }
+      if (q == (T)0 && x.g < (T)0) { q = -tau * x.g; acc[2] += (T)1; }
+      acc[0] += tabs(q - x.p);
+      a.f.p[i] = q;
+    }
+    acc[1] += q;
+    return q;
+  } else if (MODE == A_PK_T) {
+    const T tv = x.p > (T)0 ? x.g + beta * x.t : (T)0;
+    a.f.t[i] = tv;
+    return tv;
+  } else {  // A_CG_T
+    const T tv = x.s ? x.g + beta * x.t : (T)0;
+    a.f.t[i] = tv;
+    return tv;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pass A: nbA rows per CTA, M/8 threads per row.
+template <typename T, int MODE, int LOGL>
 __global__ void __launch_bounds__(1024) k_pass_a(PassArgs<T> a) {
   using Cx = C<T>;
+  using F = FftC<T, LOGL>;
+  constexpr int L = F::L, L8 = F::L8, M = L;
+  constexpr bool HALF = MODE != A_TORUS;  // conv inputs fill the first half only
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[3 * 32];
-  Cx* buf = reinterpret_cast<Cx*>(smem_raw);
+  Cx* sm = reinterpret_cast<Cx*>(smem_raw);
   Scalars* sc = a.sc;
   if (MODE != A_PLAIN && MODE != A_TORUS) {
     if (sc->done) return;
   }
-  const int M = a.pl.M, logM = a.pl.logM, nb = a.pl.nbA;
-  const int row0 = blockIdx.x * nb;
+  const int nb = a.pl.nbA, lognb = a.pl.lognbA, rs = a.pl.gA.rs;
   const int tid = threadIdx.x, nthr = blockDim.x;
+  const int b = tid >> (LOGL - 3), t = tid & (L8 - 1);
+  const int row0 = blockIdx.x * nb;
+  const int row = row0 + b;
   const int ncols = a.ncols_in, nrows = a.nrows_in;
+  const bool act = row < nrows;
   const int half = (ncols + 1) >> 1;
-  T acc0 = 0, acc1 = 0, acc2 = 0;
+  Cx* buf = sm + b * rs;
+  const Cx* tw = reinterpret_cast<const Cx*>(a.twA);
+  T acc[3] = {0, 0, 0};
   bool upd = false;
   T tau = 0, beta = 0;
   if (MODE == A_PK_P) { upd = sc->have_tau != 0; tau = (T)sc->tau; }
   if (MODE == A_PK_T || MODE == A_CG_T) beta = (T)sc->beta;
+  const size_t rowoff = (size_t)row * ncols;
 
-  for (int idx = tid; idx < nb * M; idx += nthr) {
-    const int b = idx >> logM, n = idx & (M - 1);
-    const int row = row0 + b;
-    T xv[2] = {0, 0};
-    if (row < nrows && n < half) {
+  Cx v[8];
+  if (MODE == A_TORUS) {
+    // K on the even Px x Py torus (spectrum set-up, FP64, all columns)
+    const int py = a.pl.py, px = a.pl.px;
+    const int ry = row < py - row ? row : py - row;
 #pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const int col = 2 * n + e;
-        if (col >= ncols) continue;
-        const size_t i = (size_t)row * ncols + col;
-        T x = 0;
-        if (MODE == A_PLAIN) {
-          x = a.f.src[i];
-        } else if (MODE == A_PK_P) {
-          const T pv = a.f.p[i];
-          T q = pv;
-          if (upd) {
-            if (pv > (T)0) {
-              q = pv - tau * a.f.t[i];
-              q = q > (T)0 ? q : (T)0;
-            }
-            const T gv = a.f.g[i];
-            if (q == (T)0 && gv < (T)0) { q = -tau * gv; acc2 += (T)1; }
-            acc0 += tabs(q - pv);
-            a.f.p[i] = q;
-          }
-          acc1 += q;
-          x = q;
-        } else if (MODE == A_PK_T) {
-          const T tv = a.f.p[i] > (T)0 ? a.f.g[i] + beta * a.f.t[i] : (T)0;
-          a.f.t[i] = tv;
-          x = tv;
-        } else if (MODE == A_CG_T) {
-          const T tv = a.f.S[i] ? a.f.g[i] + beta * a.f.t[i] : (T)0;
-          a.f.t[i] = tv;
-          x = tv;
-        } else if (MODE == A_TORUS) {
-          const int py = a.pl.py, px = a.pl.px;
-          const int ry = row < py - row ? row : py - row;
-          const int rx = col < px - col ? col : px - col;
-          x = (T)a.kq64[(size_t)ry * (M + 1) + rx];
-        }
-        xv[e] = x;
+    for (int e = 0; e < 8; ++e) {
+      const int n = F::n0(t, e);
+      T xv[2] = {0, 0};
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int col = 2 * n + h;
+        const int rx = col < px - col ? col : px - col;
+        if (act) xv[h] = (T)__ldg(a.kq64 + (size_t)ry * (M + 1) + rx);
       }
+      v[e] = mk<T>(xv[0], xv[1]);
     }
-    buf[(b << logM) + n] = mk<T>(xv[0], xv[1]);
+  } else {
+    PIn<T> in[8][2];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      if (HALF && !F::first_half(e)) continue;
+      const int n = F::n0(t, e);
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        if (act && n < half && 2 * n + h < ncols) pro_gather<T, MODE>(a, rowoff + 2 * n + h, in[e][h]);
+    }
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      v[e] = mk<T>(0, 0);
+      if (HALF && !F::first_half(e)) continue;
+      const int n = F::n0(t, e);
+      T xv[2] = {0, 0};
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        if (act && n < half && 2 * n + h < ncols)
+          xv[h] = pro_apply<T, MODE>(a, rowoff + 2 * n + h, in[e][h], upd, tau, beta, acc);
+      v[e] = mk<T>(xv[0], xv[1]);
+    }
   }
+  F::stage0_fwd(v, t, tw);
+#pragma unroll
+  for (int e = 0; e < 8; ++e) buf[F::ix0(t, e)] = v[e];
   __syncthreads();
-  {
-    const int per = M >> 3;
-    const int b = tid / per, j0 = tid - b * per;
-    fft_smem<T, -1>(buf + (b << logM), logM, j0);
+#pragma unroll
+  for (int ls = F::LS_TOP; ls >= 0; ls -= 3) {
+    F::dif(buf, t, ls, tw);
+    __syncthreads();
   }
   if (MODE == A_PK_P) {
-    double v[3] = {(double)acc0, (double)acc1, (double)acc2};
-    block_sum<3>(v, red);
+    double vv[3] = {(double)acc[0], (double)acc[1], (double)acc[2]};
+    block_sum<3>(vv, red);
     if (tid == 0) {
       double* pp = a.partA + 4 * blockIdx.x;
-      pp[0] = v[0]; pp[1] = v[1]; pp[2] = v[2];
+      pp[0] = vv[0]; pp[1] = vv[1]; pp[2] = vv[2];
     }
   }
-  // split the packed transform into the half spectrum and store transposed
-  const T invM = (T)1 / (T)M;
+  // split the packed transform into the half spectrum, store transposed
+  const Cx* tws = reinterpret_cast<const Cx*>(a.twS);
+  const int* sp = a.spA;
   Cx* W = reinterpret_cast<Cx*>(a.W);
-  for (int idx = tid; idx < (M + 1) * nb; idx += nthr) {
-    const int k = idx / nb, b = idx - k * nb;
-    const int row = row0 + b;
-    if (row >= nrows) continue;
-    const Cx* s = buf + (b << logM);
+#pragma unroll 3
+  for (int idx = tid; idx < (M + 1) << lognb; idx += nthr) {
+    const int k = idx >> lognb, bb = idx & (nb - 1);
+    const int rw = row0 + bb;
+    if (rw >= nrows) continue;
+    const Cx* s = sm + bb * rs;
     Cx X;
     if (k == 0 || k == M) {
       const Cx z0 = s[0];
       X = mk<T>(k == 0 ? z0.x + z0.y : z0.x - z0.y, (T)0);
     } else {
-      const Cx zk = s[k], zm = conj<T>(s[M - k]);
+      const Cx zk = s[__ldg(sp + k)];
+      const Cx zm = conj<T>(s[__ldg(sp + M - k)]);
       const Cx E = scale<T>(add<T>(zk, zm), (T)0.5);
       const Cx dlt = sub<T>(zk, zm);
       const Cx O = mk<T>((T)0.5 * dlt.y, (T)-0.5 * dlt.x);  // (zk - zm) / (2i)
-      X = add<T>(E, mul<T>(expipi(-(T)k * invM), O));
+      X = add<T>(E, mul<T>(__ldg(tws + k), O));
     }
-    W[(size_t)k * a.rows_w + row] = X;
+    W[(size_t)k * a.rows_w + rw] = X;
   }
 }
 
 // ---------------------------------------------------------------------------
-template <typename T, int MODE>
+// Pass B: nbB columns per CTA, Py/8 threads per column; columns kx = 0..M.
+template <typename T, int MODE, int LOGL>
 __global__ void __launch_bounds__(1024) k_pass_b(PassArgs<T> a) {
   using Cx = C<T>;
+  using F = FftC<T, LOGL>;
+  constexpr int L = F::L, L8 = F::L8, R0 = F::R0, hyq = (L >> 1) + 1;
+  constexpr bool HALF = MODE == B_CONV;  // Ny <= Py/2 rows in, Ny rows out
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Cx* buf = reinterpret_cast<Cx*>(smem_raw);
+  Cx* sm = reinterpret_cast<Cx*>(smem_raw);
   if (MODE == B_CONV && a.sc != nullptr) {
     if (a.sc->done) return;
   }
-  const int Py = a.pl.py, logPy = a.pl.logPy, nb = a.pl.nbB, M = a.pl.M;
-  const int rin = a.rows_w;
-  const int col0 = blockIdx.x * nb;
-  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int M = a.pl.M, rin = a.rows_w, rs = a.pl.gB.rs;
+  const int tid = threadIdx.x;
+  const int c = tid >> (LOGL - 3), t = tid & (L8 - 1);
+  const int kx = blockIdx.x * a.pl.nbB + c;
+  const bool act = kx <= M;
+  Cx* buf = sm + c * rs;
+  const Cx* tw = reinterpret_cast<const Cx*>(a.twB);
+  const int* sp = a.spB;
   Cx* W = reinterpret_cast<Cx*>(a.W);
-  for (int idx = tid; idx < nb * Py; idx += nthr) {
-    const int c = idx >> logPy, y = idx & (Py - 1);
-    const int kx = col0 + c;
-    Cx v = mk<T>(0, 0);
-    if (kx < M && y < rin) {
-      if (kx == 0) v = mk<T>(W[y].x, W[(size_t)M * rin + y].x);
-      else v = W[(size_t)kx * rin + y];
-    }
-    buf[(c << logPy) + y] = v;
+  const size_t coff = (size_t)(act ? kx : 0) * rin;
+
+  Cx v[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    v[e] = mk<T>(0, 0);
+    if (HALF && !F::first_half(e)) continue;
+    const int y = F::n0(t, e);
+    if (act && y < rin) v[e] = W[coff + y];
   }
+  F::stage0_fwd(v, t, tw);
+#pragma unroll
+  for (int e = 0; e < 8; ++e) buf[F::ix0(t, e)] = v[e];
   __syncthreads();
-  const int per = Py >> 3;
-  const int bseq = tid / per, j0 = tid - bseq * per;
-  fft_smem<T, -1>(buf + (bseq << logPy), logPy, j0);
-  const int hy = Py >> 1, hyq = hy + 1;
+#pragma unroll
+  for (int ls = F::LS_TOP; ls >= 3; ls -= 3) {
+    F::dif(buf, t, ls, tw);
+    __syncthreads();
+  }
   if (MODE == B_SPECTRUM) {
-    for (int idx = tid; idx < nb * hyq; idx += nthr) {
-      const int c = idx / hyq, ky = idx - c * hyq;
-      const int kx = col0 + c;
-      if (kx >= M) continue;
-      const Cx* s = buf + (c << logPy);
-      const Cx v1 = s[ky], v2 = s[(Py - ky) & (Py - 1)];
-      if (kx == 0) {
-        const double re0 = 0.5 * ((double)v1.x + (double)v2.x);  // Re (v1 + conj v2)/2
-        const double reM = 0.5 * ((double)v1.y + (double)v2.y);  // Re (v1 - conj v2)/(2i)
-        a.khat64_out[ky] = re0;
-        a.khat64_out[(size_t)M * hyq + ky] = reM;
-        a.khat32_out[ky] = (float)re0;
-        a.khat32_out[(size_t)M * hyq + ky] = (float)reM;
-      } else {
-        a.khat64_out[(size_t)kx * hyq + ky] = (double)v1.x;
-        a.khat32_out[(size_t)kx * hyq + ky] = (float)v1.x;
-      }
+    F::dif(buf, t, 0, tw);
+    __syncthreads();
+    if (!act) return;
+    for (int ky = t; ky < hyq; ky += L8) {
+      const double re = (double)buf[__ldg(sp + ky)].x;
+      a.khat64_out[(size_t)kx * hyq + ky] = re;
+      a.khat32_out[(size_t)kx * hyq + ky] = (float)re;
     }
     return;
   }
-  // multiply by the real, even spectrum; pairs (ky, Py-ky) handled together
-  for (int idx = tid; idx < nb * hyq; idx += nthr) {
-    const int c = idx / hyq, ky = idx - c * hyq;
-    const int kx = col0 + c;
-    if (kx >= M) continue;
-    Cx* s = buf + (c << logPy);
-    const int ky2 = (Py - ky) & (Py - 1);
-    if (kx == 0) {
-      const Cx v1 = s[ky], v2 = s[ky2];
-      const T k0 = a.khat[ky], kM = a.khat[(size_t)M * hyq + ky];
-      // v = A + iB with A, B the spectra of columns 0 and M
-      const Cx Av = scale<T>(add<T>(v1, conj<T>(v2)), (T)0.5);
-      const Cx dd = sub<T>(v1, conj<T>(v2));
-      const Cx Bv = mk<T>((T)0.5 * dd.y, (T)-0.5 * dd.x);
-      const Cx n1 = add<T>(scale<T>(Av, k0), mul_si<T, 1>(scale<T>(Bv, kM)));
-      const Cx n2 = add<T>(scale<T>(conj<T>(Av), k0), mul_si<T, 1>(scale<T>(conj<T>(Bv), kM)));
-      s[ky] = n1;
-      if (ky2 != ky) s[ky2] = n2;
-    } else {
-      const T kf = a.khat[(size_t)kx * hyq + ky];
-      s[ky] = scale<T>(s[ky], kf);
-      if (ky2 != ky) s[ky2] = scale<T>(s[ky2], kf);
+  // last DIF stage (stride 1), spectrum multiply, first DIT stage (stride 1),
+  // in registers.  Thread t takes the group holding frequencies t + q L/8.
+  {
+    const int sp0 = __ldg(sp + t);
+    const T* kc = a.khat + (size_t)(act ? kx : 0) * hyq;
+    T kf[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int ky = t + q * L8;
+      const int kk = ky <= (L >> 1) ? ky : L - ky;
+      kf[q] = act ? __ldg(kc + kk) : (T)0;
     }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) v[r] = buf[sp0 ^ r];
+    dft8<T, -1>(v);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = scale<T>(v[q], kf[q]);
+    dft8<T, 1>(v);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) buf[sp0 ^ r] = v[r];
   }
   __syncthreads();
-  fft_smem<T, 1>(buf + (bseq << logPy), logPy, j0);
-  for (int idx = tid; idx < nb * rin; idx += nthr) {
-    const int c = idx / rin, y = idx - c * rin;
-    const int kx = col0 + c;
-    if (kx >= M) continue;
-    const Cx v = buf[(c << logPy) + y];
-    if (kx == 0) {
-      W[y] = mk<T>(v.x, (T)0);
-      W[(size_t)M * rin + y] = mk<T>(v.y, (T)0);
-    } else {
-      W[(size_t)kx * rin + y] = v;
+#pragma unroll
+  for (int ls = 3; ls <= F::LS_TOP; ls += 3) {
+    F::dit(buf, t, ls, tw);
+    __syncthreads();
+  }
+  // last DIT stage (inverse of stage 0), natural order, first half to global
+#pragma unroll
+  for (int e = 0; e < 8; ++e) v[e] = buf[F::ix0(t, e)];
+  F::stage0_inv(v, t, tw);
+  if (act) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      if (!F::first_half(e)) continue;
+      const int y = F::n0(t, e);
+      if (y < rin) W[coff + y] = v[e];
     }
   }
+  (void)R0;
 }
 
 // ---------------------------------------------------------------------------
+// Pass C epilogue, in two phases like the prologue.
+template <typename T>
+struct EIn {
+  T c, p, t, g;
+  uint8_t s;
+};
+
 template <typename T, int MODE>
+__device__ __forceinline__ void epi_gather(const PassArgs<T>& a, size_t i, EIn<T>& x) {
+  if (MODE == C_PK_G) {
+    x.c = a.f.c[i]; x.p = a.f.p[i];
+  } else if (MODE == C_PK_R) {
+    x.p = a.f.p[i]; x.t = a.f.t[i]; x.g = a.f.g[i];
+  } else if (MODE == C_CG_R) {
+    x.s = a.f.S[i]; x.t = a.f.t[i];
+  } else if (MODE == C_CG_G) {
+    x.s = a.f.S[i]; x.c = a.f.c[i];
+  } else if (MODE == C_GAP) {
+    x.c = a.f.c[i];
+  }
+}
+
+template <typename T, int MODE>
+__device__ __forceinline__ void epi_apply(const PassArgs<T>& a, size_t i, T u, const EIn<T>& x, T* acc) {
+  if (MODE == C_PLAIN) {
+    a.f.dst[i] = u;
+  } else if (MODE == C_PK_G) {
+    const T gv = u + x.c;
+    a.f.g[i] = gv;
+    if (x.p > (T)0) { acc[0] += gv * gv; acc[1] += (T)1; }
+  } else if (MODE == C_PK_R) {
+    if (x.p > (T)0) { acc[0] += x.g * x.t; acc[1] += u * x.t; }
+  } else if (MODE == C_CG_R) {
+    const T rv = x.s ? u : (T)0;
+    a.f.r[i] = rv;
+    acc[0] += rv * x.t;
+  } else if (MODE == C_CG_G) {
+    if (x.s) {
+      const T gv = u + x.c;
+      a.f.g[i] = gv;
+      acc[0] += gv * gv;
+      acc[1] += x.c * x.c;
+    } else {
+      a.f.g[i] = (T)0;
+    }
+  } else if (MODE == C_GAP) {
+    a.f.g[i] = u + x.c;
+  }
+}
+
+template <typename T, int MODE, int LOGL>
 __global__ void __launch_bounds__(1024) k_pass_c(PassArgs<T> a) {
   using Cx = C<T>;
+  using F = FftC<T, LOGL>;
+  constexpr int L = F::L, L8 = F::L8, M = L;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[3 * 32];
   __shared__ int lastflag;
-  Cx* buf = reinterpret_cast<Cx*>(smem_raw);
+  Cx* sm = reinterpret_cast<Cx*>(smem_raw);
   Scalars* sc = a.sc;
   if (MODE != C_PLAIN && MODE != C_GAP) {
     if (sc->done) return;
   }
-  const int M = a.pl.M, logM = a.pl.logM, nb = a.pl.nbA, ld = M + 1;
+  const int nb = a.pl.nbA, lognb = a.pl.lognbA, rs = a.pl.gA.rs;
   const int nx = a.pl.nx, ny = a.pl.ny;
-  const int row0 = blockIdx.x * nb;
   const int tid = threadIdx.x, nthr = blockDim.x;
+  const int b = tid >> (LOGL - 3), t = tid & (L8 - 1);
+  const int row0 = blockIdx.x * nb;
   const Cx* W = reinterpret_cast<const Cx*>(a.W);
-  for (int idx = tid; idx < (M + 1) * nb; idx += nthr) {
-    const int k = idx / nb, b = idx - k * nb;
-    const int row = row0 + b;
-    buf[b * ld + k] = row < ny ? W[(size_t)k * a.rows_w + row] : mk<T>(0, 0);
-  }
-  __syncthreads();
-  // rebuild the packed half-length spectrum: Z[k] = E + i O with
-  // E = X[k] + conj X[M-k],  O = (X[k] - conj X[M-k]) exp(+2 pi i k / Px)
-  const T invM = (T)1 / (T)M;
-  const int hm = (M >> 1) + 1;
-  for (int idx = tid; idx < nb * hm; idx += nthr) {
-    const int b = idx / hm, k = idx - b * hm;
-    Cx* s = buf + b * ld;
-    const Cx xk = s[k], xm = s[M - k];
-    const Cx wk = expipi((T)k * invM);
-    {
-      const Cx E = add<T>(xk, conj<T>(xm));
-      const Cx O = mul<T>(sub<T>(xk, conj<T>(xm)), wk);
-      s[k] = add<T>(E, mul_si<T, 1>(O));
-    }
-    if (k != 0 && k != M - k) {
-      const Cx wm = mk<T>(-wk.x, wk.y);  // exp(+2 pi i (M-k)/Px) = -conj(wk)
-      const Cx E = add<T>(xm, conj<T>(xk));
-      const Cx O = mul<T>(sub<T>(xm, conj<T>(xk)), wm);
-      s[M - k] = add<T>(E, mul_si<T, 1>(O));
-    }
-  }
-  __syncthreads();
+  const Cx* tws = reinterpret_cast<const Cx*>(a.twS);
+  const Cx* tw = reinterpret_cast<const Cx*>(a.twA);
+  const int* sp = a.spA;
+  // rebuild the packed half-length spectrum, scattered to digit-reversed
+  // positions: Z[k] = E + i O, E = X[k] + conj X[M-k], O = (X[k] - conj X[M-k]) e^{+i pi k/M}.
+  // Each thread handles up to NP pairs (k, M-k); all loads are issued first.
   {
-    const int per = M >> 3;
-    const int b = tid / per, j0 = tid - b * per;
-    fft_smem<T, 1>(buf + b * ld, logM, j0);
-  }
-  const T us = (T)a.uscale;
-  T acc0 = 0, acc1 = 0;
-  T beta_unused = 0;
-  (void)beta_unused;
-  for (int idx = tid; idx < nb * M; idx += nthr) {
-    const int b = idx >> logM, n = idx & (M - 1);
-    const int row = row0 + b;
-    if (row >= ny) continue;
-    const Cx z = buf[b * ld + n];
+    constexpr int hm = (M >> 1) + 1;
+    const int total = hm << lognb;
+    constexpr int NP = 5;  // ceil((M/2 + 1) nb / (nb M/8)) for M >= 16
+    Cx xk[NP], xm[NP];
 #pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const int col = 2 * n + e;
-      if (col >= nx) continue;
-      const size_t i = (size_t)row * nx + col;
-      const T u = us * (e ? z.y : z.x);
-      if (MODE == C_PLAIN) {
-        a.f.dst[i] = u;
-      } else if (MODE == C_PK_G) {
-        const T gv = u + a.f.c[i];
-        a.f.g[i] = gv;
-        if (a.f.p[i] > (T)0) { acc0 += gv * gv; acc1 += (T)1; }
-      } else if (MODE == C_PK_R) {
-        if (a.f.p[i] > (T)0) {
-          const T tv = a.f.t[i];
-          acc0 += a.f.g[i] * tv;
-          acc1 += u * tv;
+    for (int j = 0; j < NP; ++j) {
+      const int idx = tid + j * nthr;
+      xk[j] = mk<T>(0, 0);
+      xm[j] = mk<T>(0, 0);
+      if (idx < total) {
+        const int k = idx >> lognb, rw = row0 + (idx & (nb - 1));
+        if (rw < ny) {
+          xk[j] = W[(size_t)k * a.rows_w + rw];
+          xm[j] = W[(size_t)(M - k) * a.rows_w + rw];
         }
-      } else if (MODE == C_CG_R) {
-        const T rv = a.f.S[i] ? u : (T)0;
-        a.f.r[i] = rv;
-        acc0 += rv * a.f.t[i];
-      } else if (MODE == C_CG_G) {
-        if (a.f.S[i]) {
-          const T cv = a.f.c[i];
-          const T gv = u + cv;
-          a.f.g[i] = gv;
-          acc0 += gv * gv;
-          acc1 += cv * cv;
-        } else {
-          a.f.g[i] = (T)0;
-        }
-      } else if (MODE == C_GAP) {
-        a.f.g[i] = u + a.f.c[i];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      const int idx = tid + j * nthr;
+      if (idx >= total) continue;
+      const int k = idx >> lognb, bb = idx & (nb - 1);
+      Cx* s = sm + bb * rs;
+      const Cx wk = conj<T>(__ldg(tws + k));
+      {
+        const Cx E = add<T>(xk[j], conj<T>(xm[j]));
+        const Cx O = mul<T>(sub<T>(xk[j], conj<T>(xm[j])), wk);
+        s[__ldg(sp + k)] = add<T>(E, mul_si<T, 1>(O));
+      }
+      if (k != 0 && k != M - k) {
+        const Cx wm = mk<T>(-wk.x, wk.y);  // exp(+i pi (M-k)/M) = -conj(wk)
+        const Cx E = add<T>(xm[j], conj<T>(xk[j]));
+        const Cx O = mul<T>(sub<T>(xm[j], conj<T>(xk[j])), wm);
+        s[__ldg(sp + M - k)] = add<T>(E, mul_si<T, 1>(O));
       }
     }
   }
+  __syncthreads();
+  Cx* buf = sm + b * rs;
+#pragma unroll
+  for (int ls = 0; ls <= F::LS_TOP; ls += 3) {
+    F::dit(buf, t, ls, tw);
+    __syncthreads();
+  }
+  // last DIT stage: natural-order outputs z[n] = (x[2n], x[2n+1]) * Px; the
+  // epilogue fields are gathered first so their loads overlap the stage
+  const T us = (T)a.uscale;
+  T acc[3] = {0, 0, 0};
+  const int row = row0 + b;
+  const bool act = row < ny;
+  const size_t rowoff = (size_t)row * nx;
+  const int half = (nx + 1) >> 1;
+  EIn<T> ein[8][2];
+  if (MODE != C_PLAIN) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      if (!F::first_half(e)) continue;
+      const int n = F::n0(t, e);
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        if (act && n < half && 2 * n + h < nx) epi_gather<T, MODE>(a, rowoff + 2 * n + h, ein[e][h]);
+    }
+  }
+  Cx v[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) v[e] = buf[F::ix0(t, e)];
+  F::stage0_inv(v, t, tw);
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    if (!F::first_half(e)) continue;
+    const int n = F::n0(t, e);
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+      if (act && n < half && 2 * n + h < nx)
+        epi_apply<T, MODE>(a, rowoff + 2 * n + h, us * (h ? v[e].y : v[e].x), ein[e][h], acc);
+  }
   if (MODE == C_PLAIN || MODE == C_GAP) return;
-  double v[2] = {(double)acc0, (double)acc1};
-  block_sum<2>(v, red);
+  double vv[2] = {(double)acc[0], (double)acc[1]};
+  block_sum<2>(vv, red);
   if (tid == 0) {
     double* pp = a.partC + 4 * blockIdx.x;
-    pp[0] = v[0]; pp[1] = v[1];
+    pp[0] = vv[0]; pp[1] = vv[1];
   }
   if (!last_block_arrival(MODE == C_PK_G ? &sc->cnt_c : &sc->cnt_a, &lastflag)) return;
   double s2[2];
@@ -377,7 +619,13 @@ __global__ void __launch_bounds__(1024) k_pass_c(PassArgs<T> a) {
     const double sgt = s2[0], srt = s2[1];
     if (!isfinite(sgt) || !isfinite(srt)) { sc->status = SC_NUMERIC; sc->done = 1; }
     else if (srt == 0.0) { sc->done = 1; }
-    else { sc->tau = sgt / srt; sc->have_tau = 1; }
+    else if (!(sgt > 0.0) || srt < 0.0) {
+      // finite precision lost the conjugacy (tau would be <= 0 and the overlap
+      // step p = -tau g would go negative): skip this update and restart the
+      // directions from the gap (delta = 0)
+      sc->have_tau = 0;
+      sc->delta = 0.0;
+    } else { sc->tau = sgt / srt; sc->have_tau = 1; }
   } else if (MODE == C_CG_R) {
     sc->cnt_a = 0;
     const double str = s2[0];
@@ -540,66 +788,109 @@ __global__ void k_mask_field(T* x, const uint8_t* S, size_t n) {
 }
 
 // ---------------------------------------------------------------------------
-// Host launchers
+// Host launchers: dispatch on the transform length.
 
-template <typename T>
-void launch_pass_a(const PassArgs<T>& a, int mode, cudaStream_t s) {
+#define BEM_LOGL_CASES_A(X) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12)
+#define BEM_LOGL_CASES_B(X) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13)
+
+template <typename T, int MODE>
+void launch_a_mode(const PassArgs<T>& a, cudaStream_t s) {
   const dim3 grid((a.nrows_in + a.pl.nbA - 1) / a.pl.nbA), block(a.pl.threadsA);
-  switch (mode) {
-    case A_PLAIN: k_pass_a<T, A_PLAIN><<<grid, block, a.pl.smemA, s>>>(a); break;
-    case A_PK_P: k_pass_a<T, A_PK_P><<<grid, block, a.pl.smemA, s>>>(a); break;
-    case A_PK_T: k_pass_a<T, A_PK_T><<<grid, block, a.pl.smemA, s>>>(a); break;
-    case A_CG_T: k_pass_a<T, A_CG_T><<<grid, block, a.pl.smemA, s>>>(a); break;
-    case A_TORUS:
-      if constexpr (sizeof(T) == 8) k_pass_a<T, A_TORUS><<<grid, block, a.pl.smemA, s>>>(a);
-      break;
+  switch (a.pl.gA.logL) {
+#define BEM_CASE(LG) case LG: k_pass_a<T, MODE, LG><<<grid, block, a.pl.smemA, s>>>(a); break;
+    BEM_LOGL_CASES_A(BEM_CASE)
+#undef BEM_CASE
+  }
+}
+template <typename T, int MODE>
+void launch_b_mode(const PassArgs<T>& a, cudaStream_t s) {
+  const dim3 grid(a.pl.gridB), block(a.pl.threadsB);
+  switch (a.pl.gB.logL) {
+#define BEM_CASE(LG) case LG: k_pass_b<T, MODE, LG><<<grid, block, a.pl.smemB, s>>>(a); break;
+    BEM_LOGL_CASES_B(BEM_CASE)
+#undef BEM_CASE
+  }
+}
+template <typename T, int MODE>
+void launch_c_mode(const PassArgs<T>& a, cudaStream_t s) {
+  const dim3 grid(a.pl.gridA), block(a.pl.threadsA);
+  switch (a.pl.gA.logL) {
+#define BEM_CASE(LG) case LG: k_pass_c<T, MODE, LG><<<grid, block, a.pl.smemC, s>>>(a); break;
+    BEM_LOGL_CASES_A(BEM_CASE)
+#undef BEM_CASE
   }
 }
 
 template <typename T>
-void launch_pass_b(const PassArgs<T>& a, int mode, cudaStream_t s) {
-  const dim3 grid(a.pl.gridB), block(a.pl.threadsB);
-  if (mode == B_SPECTRUM) k_pass_b<T, B_SPECTRUM><<<grid, block, a.pl.smemB, s>>>(a);
-  else k_pass_b<T, B_CONV><<<grid, block, a.pl.smemB, s>>>(a);
+void launch_pass_a(const PassArgs<T>& a, int mode, cudaStream_t s) {
+  switch (mode) {
+    case A_PLAIN: launch_a_mode<T, A_PLAIN>(a, s); break;
+    case A_PK_P: launch_a_mode<T, A_PK_P>(a, s); break;
+    case A_PK_T: launch_a_mode<T, A_PK_T>(a, s); break;
+    case A_CG_T: launch_a_mode<T, A_CG_T>(a, s); break;
+    case A_TORUS:
+      if constexpr (sizeof(T) == 8) launch_a_mode<T, A_TORUS>(a, s);
+      break;
+  }
 }
-
+template <typename T>
+void launch_pass_b(const PassArgs<T>& a, int mode, cudaStream_t s) {
+  if (mode == B_SPECTRUM) launch_b_mode<T, B_SPECTRUM>(a, s);
+  else launch_b_mode<T, B_CONV>(a, s);
+}
 template <typename T>
 void launch_pass_c(const PassArgs<T>& a, int mode, cudaStream_t s) {
-  const dim3 grid(a.pl.gridA), block(a.pl.threadsA);
   switch (mode) {
-    case C_PLAIN: k_pass_c<T, C_PLAIN><<<grid, block, a.pl.smemC, s>>>(a); break;
-    case C_PK_G: k_pass_c<T, C_PK_G><<<grid, block, a.pl.smemC, s>>>(a); break;
-    case C_PK_R: k_pass_c<T, C_PK_R><<<grid, block, a.pl.smemC, s>>>(a); break;
-    case C_CG_R: k_pass_c<T, C_CG_R><<<grid, block, a.pl.smemC, s>>>(a); break;
-    case C_CG_G: k_pass_c<T, C_CG_G><<<grid, block, a.pl.smemC, s>>>(a); break;
-    case C_GAP: k_pass_c<T, C_GAP><<<grid, block, a.pl.smemC, s>>>(a); break;
+    case C_PLAIN: launch_c_mode<T, C_PLAIN>(a, s); break;
+    case C_PK_G: launch_c_mode<T, C_PK_G>(a, s); break;
+    case C_PK_R: launch_c_mode<T, C_PK_R>(a, s); break;
+    case C_CG_R: launch_c_mode<T, C_CG_R>(a, s); break;
+    case C_CG_G: launch_c_mode<T, C_CG_G>(a, s); break;
+    case C_GAP: launch_c_mode<T, C_GAP>(a, s); break;
   }
 }
 
 // Opt every pass kernel into `bytes` of dynamic shared memory (the static
 // reduction scratch counts against the same 227 KB per block, so the request
 // is sized to what the plans need).  Returns the first failure.
+#define BEM_ATTR(fn) \
+  if ((r = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess && e == cudaSuccess) e = r;
 template <typename T>
-cudaError_t set_smem_attrs(int bytes) {
-  const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+cudaError_t set_smem_attrs_a(int bytes) {
   cudaError_t e = cudaSuccess, r;
-#define BEM_ATTR(fn) if ((r = cudaFuncSetAttribute(fn, at, bytes)) != cudaSuccess && e == cudaSuccess) e = r
-  BEM_ATTR((k_pass_a<T, A_PLAIN>));
-  BEM_ATTR((k_pass_a<T, A_PK_P>));
-  BEM_ATTR((k_pass_a<T, A_PK_T>));
-  BEM_ATTR((k_pass_a<T, A_CG_T>));
-  if constexpr (sizeof(T) == 8) BEM_ATTR((k_pass_a<T, A_TORUS>));
-  BEM_ATTR((k_pass_b<T, B_CONV>));
-  BEM_ATTR((k_pass_b<T, B_SPECTRUM>));
-  BEM_ATTR((k_pass_c<T, C_PLAIN>));
-  BEM_ATTR((k_pass_c<T, C_PK_G>));
-  BEM_ATTR((k_pass_c<T, C_PK_R>));
-  BEM_ATTR((k_pass_c<T, C_CG_R>));
-  BEM_ATTR((k_pass_c<T, C_CG_G>));
-  BEM_ATTR((k_pass_c<T, C_GAP>));
-#undef BEM_ATTR
+#define BEM_CASE(LG)                          \
+  BEM_ATTR((k_pass_a<T, A_PLAIN, LG>))        \
+  BEM_ATTR((k_pass_a<T, A_PK_P, LG>))         \
+  BEM_ATTR((k_pass_a<T, A_PK_T, LG>))         \
+  BEM_ATTR((k_pass_a<T, A_CG_T, LG>))         \
+  if constexpr (sizeof(T) == 8) { BEM_ATTR((k_pass_a<T, A_TORUS, LG>)) }
+  BEM_LOGL_CASES_A(BEM_CASE)
+#undef BEM_CASE
   return e;
 }
+template <typename T>
+cudaError_t set_smem_attrs_b(int bytes) {
+  cudaError_t e = cudaSuccess, r;
+#define BEM_CASE(LG) BEM_ATTR((k_pass_b<T, B_CONV, LG>)) BEM_ATTR((k_pass_b<T, B_SPECTRUM, LG>))
+  BEM_LOGL_CASES_B(BEM_CASE)
+#undef BEM_CASE
+  return e;
+}
+template <typename T>
+cudaError_t set_smem_attrs_c(int bytes) {
+  cudaError_t e = cudaSuccess, r;
+#define BEM_CASE(LG)                          \
+  BEM_ATTR((k_pass_c<T, C_PLAIN, LG>))        \
+  BEM_ATTR((k_pass_c<T, C_PK_G, LG>))         \
+  BEM_ATTR((k_pass_c<T, C_PK_R, LG>))         \
+  BEM_ATTR((k_pass_c<T, C_CG_R, LG>))         \
+  BEM_ATTR((k_pass_c<T, C_CG_G, LG>))         \
+  BEM_ATTR((k_pass_c<T, C_GAP, LG>))
+  BEM_LOGL_CASES_A(BEM_CASE)
+#undef BEM_CASE
+  return e;
+}
+#undef BEM_ATTR
 
 static inline int ew_grid(size_t n) {
   size_t g = (n + 255) / 256;
@@ -650,10 +941,16 @@ void launch_mask_field(T* x, const uint8_t* S, size_t n, cudaStream_t s) {
   k_mask_field<T><<<ew_grid(n), 256, 0, s>>>(x, S, n);
 }
 
-#define BEM_INSTANTIATE(T)                                                                     \
+#define BEM_INSTANTIATE_A(T)                                                                   \
   template void launch_pass_a<T>(const PassArgs<T>&, int, cudaStream_t);                      \
+  template cudaError_t set_smem_attrs_a<T>(int);
+#define BEM_INSTANTIATE_B(T)                                                                   \
   template void launch_pass_b<T>(const PassArgs<T>&, int, cudaStream_t);                      \
+  template cudaError_t set_smem_attrs_b<T>(int);
+#define BEM_INSTANTIATE_C(T)                                                                   \
   template void launch_pass_c<T>(const PassArgs<T>&, int, cudaStream_t);                      \
+  template cudaError_t set_smem_attrs_c<T>(int);
+#define BEM_INSTANTIATE_EW(T)                                                                  \
   template void launch_pk_init<T>(const Plan&, const double*, double, T*, T*, T*, int, int,    \
                                   cudaStream_t);                                               \
   template void launch_cg_update<T>(const Plan&, Fields<T>, double*, Scalars*, int,            \

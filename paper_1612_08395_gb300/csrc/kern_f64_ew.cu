@@ -1,0 +1,107 @@
+// FP64 instantiation of the elementwise kernels and the FP64 helpers of the
+// refinement sweep, twiddle and index tables.
+#include "conv_kernels.cuh"
+
+namespace bem {
+BEM_INSTANTIATE_EW(double)
+
+// p64 += dscale * dp on S (FP32 correction), optionally projected onto p >= 0.
+__global__ void k_refine_apply(double* p64, const float* dp, double dscale, const uint8_t* S,
+                               int project, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    if (!S[i]) continue;
+    double v = p64[i] + dscale * (double)dp[i];
+    if (project && v < 0.0) v = 0.0;
+    p64[i] = v;
+  }
+}
+void launch_refine_apply(double* p64, const float* dp, double dscale, const uint8_t* S, int project,
+                         size_t n, cudaStream_t s) {
+  k_refine_apply<<<ew_grid(n), 256, 0, s>>>(p64, dp, dscale, S, project, n);
+}
+
+__global__ void k_to_f32_scaled(const double* src, double scale, float* dst, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = (float)(scale * src[i]);
+}
+void launch_to_f32_scaled(const double* src, double scale, float* dst, size_t n, cudaStream_t s) {
+  k_to_f32_scaled<<<ew_grid(n), 256, 0, s>>>(src, scale, dst, n);
+}
+
+__global__ void k_to_f32(const double* src, float* dst, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
+}
+void launch_to_f32(const double* src, float* dst, size_t n, cudaStream_t s) {
+  k_to_f32<<<ew_grid(n), 256, 0, s>>>(src, dst, n);
+}
+
+// Stage twiddle tables of a length 2^logL transform: stages in DIF order,
+// the table of stage (R, s) holds exp(-2 pi i o/(R s)) for o < s, tables
+// concatenated (the radix-8 offsets are tw_off8).  Computed in FP64.
+__global__ void k_twiddles(double2* t64, float2* t32, int logL) {
+  const int r0 = logL % 3;
+  const int L = 1 << logL;
+  int off = 0;
+  int R = r0 ? (1 << r0) : 8;
+  int s = L / R;
+  for (;;) {
+    for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < s; o += gridDim.x * blockDim.x) {
+      double sn, cs;
+      sincospi(-2.0 * (double)o / ((double)R * (double)s), &sn, &cs);
+      t64[off + o] = make_double2(cs, sn);
+      t32[off + o] = make_float2((float)cs, (float)sn);
+    }
+    if (s == 1) break;
+    off += s;
+    R = 8;
+    s /= 8;
+  }
+}
+void launch_twiddles(double2* t64, float2* t32, int logL, cudaStream_t s) {
+  k_twiddles<<<64, 256, 0, s>>>(t64, t32, logL);
+}
+
+// exp(-i pi k / M), k = 0..M: the real-FFT split of a length-2M real transform.
+__global__ void k_split_twiddles(double2* t64, float2* t32, int M) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= M; k += gridDim.x * blockDim.x) {
+    double sn, cs;
+    sincospi(-(double)k / (double)M, &sn, &cs);
+    t64[k] = make_double2(cs, sn);
+    t32[k] = make_float2((float)cs, (float)sn);
+  }
+}
+void launch_split_twiddles(double2* t64, float2* t32, int M, cudaStream_t s) {
+  k_split_twiddles<<<64, 256, 0, s>>>(t64, t32, M);
+}
+
+// Index tables of one transform length: so[ls*8 + r] = swz(r << ls) and
+// sp[k] = swz(dig_pos(k)) (see Geo).
+__global__ void k_geo_tables(int* so, int* sp, Geo g, int esize) {
+  const Swz z{g.sa, g.sb, g.sc, g.sd};
+  const int L = 1 << g.logL;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kSoEntries + L; i += gridDim.x * blockDim.x) {
+    int x;
+    if (i < kSoEntries) {
+      const int ls = i >> 3, r = i & 7;
+      x = (r << ls) < L ? (r << ls) : 0;
+    } else {
+      x = dig_pos(i - kSoEntries, g.logL, g.r0);
+    }
+    const int v = esize == 4 ? swz<float>(x, z) : swz<double>(x, z);
+    if (i < kSoEntries) so[i] = v;
+    else sp[i - kSoEntries] = v;
+  }
+}
+void launch_geo_tables(int* so, int* sp, Geo g, int esize, cudaStream_t s) {
+  k_geo_tables<<<32, 256, 0, s>>>(so, sp, g, esize);
+}
+
+__global__ void k_active_set(const double* p, const double* g, uint8_t* S, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    S[i] = (p[i] > 0.0 || g[i] < 0.0) ? 1 : 0;
+}
+void launch_active_set(const double* p, const double* g, uint8_t* S, size_t n, cudaStream_t s) {
+  k_active_set<<<ew_grid(n), 256, 0, s>>>(p, g, S, n);
+}
+}  // namespace bem

@@ -6,8 +6,8 @@
 // whose device memory is owned by a pool or arena the caller must not bypass,
 // and latency-critical loops where cudaMalloc's implicit device-wide
 // synchronisation is not allowed.  This entry point allocates nothing: the
-// scratch the three transform passes need (the transposed half spectrum W and
-// a transposed copy of the kernel spectrum) lives in one file-scope device
+// scratch the three transform passes need (the transposed half spectrum W, a
+// transposed copy of the kernel spectrum, the twiddle and index tables) lives in one file-scope device
 // array of kScratchBytes bytes, which every GPU that loads the library holds
 // until the process exits.
 //
@@ -19,7 +19,8 @@
 //
 // Every call shares the array and it keeps the previous call's contents.
 // Nothing in it needs clearing: each call writes every element it later reads
-// (the transposed spectrum and all of W) before reading it.  Calls whose work
+// (the spectrum copy, the twiddle and index tables and all of W) before
+// reading it.  Calls whose work
 // overlaps on the GPU (different streams, or different host threads) race on
 // the array and must be serialised by the caller.
 #include <mutex>
@@ -92,32 +93,39 @@ extern "C" int bem_convolve_noalloc(const double* khat, int Nx, int Ny, double c
     }
     base = g_scratch_dev[dev];
   }
-  const int px = pow2_at_least(2 * Nx < 16 ? 16 : 2 * Nx);
-  const int py = pow2_at_least(2 * Ny < 16 ? 16 : 2 * Ny);
+  const int px = pow2_at_least(2 * Nx < 32 ? 32 : 2 * Nx);
+  const int py = pow2_at_least(2 * Ny < 32 ? 32 : 2 * Ny);
   const int M = px / 2, hx = M + 1, hyq = py / 2 + 1;
+  // scratch layout: W | transposed spectrum | FP64 twiddles | FP32 twiddles
+  const size_t ntw = (size_t)M + py + M + 1;
   const size_t w_bytes = sizeof(double) * 2 * (size_t)hx * Ny;
-  const size_t k_bytes = sizeof(double) * (size_t)hx * hyq;
   const size_t k_off = (w_bytes + 255) & ~(size_t)255;
-  if (k_off + k_bytes > kScratchBytes)
+  const size_t t_off = (k_off + sizeof(double) * (size_t)hx * hyq + 255) & ~(size_t)255;
+  const size_t t32_off = (t_off + sizeof(double2) * ntw + 255) & ~(size_t)255;
+  const size_t g_off = (t32_off + sizeof(float2) * ntw + 255) & ~(size_t)255;
+  const size_t g_ints = 2 * bem::kSoEntries + (size_t)M + py;
+  if (g_off + sizeof(int) * g_ints > kScratchBytes)
     return bem::set_error(BEM_EINVAL, "bem_convolve_noalloc: grid needs more than the 2 MiB static scratch");
 
   // launch geometry: the same rules as the handle's FP64 plan
   bem::Plan pl{};
   pl.nx = Nx; pl.ny = Ny; pl.px = px; pl.py = py; pl.M = M;
-  pl.logM = ilog2i(M); pl.logPy = ilog2i(py);
   const int tr = M / 8;
   int nb = 256 / tr;
   if (nb < 2) nb = 2;
   while (nb > 1 && nb * tr > 1024) nb >>= 1;
-  while (nb > 1 && (size_t)nb * (M + 1) * 16 > 128 * 1024) nb >>= 1;
-  pl.nbA = nb; pl.threadsA = nb * tr; pl.gridA = (Ny + nb - 1) / nb;
-  pl.smemA = (size_t)nb * M * 16; pl.smemC = (size_t)nb * (M + 1) * 16;
+  while (nb > 1 && (size_t)nb * (M + 32) * 16 > 128 * 1024) nb >>= 1;
+  pl.nbA = nb; pl.lognbA = ilog2i(nb);
+  pl.gA = bem::make_geo(ilog2i(M), nb, 8);
+  pl.threadsA = nb * tr; pl.gridA = (Ny + nb - 1) / nb;
+  pl.smemA = (size_t)nb * pl.gA.rs * 16; pl.smemC = pl.smemA;
   const int tb = py / 8;
   int nbb = 256 / tb;
   if (nbb < 1) nbb = 1;
-  while (nbb > 1 && (size_t)nbb * py * 16 > 128 * 1024) nbb >>= 1;
-  pl.nbB = nbb; pl.threadsB = nbb * tb; pl.gridB = (M + nbb - 1) / nbb;
-  pl.smemB = (size_t)nbb * py * 16;
+  while (nbb > 1 && (size_t)nbb * (py + 32) * 16 > 128 * 1024) nbb >>= 1;
+  pl.nbB = nbb; pl.gB = bem::make_geo(ilog2i(py), nbb, 8);
+  pl.threadsB = nbb * tb; pl.gridB = (M + 1 + nbb - 1) / nbb;
+  pl.smemB = (size_t)nbb * pl.gB.rs * 16;
   // every pass stays within the default 48 KB of dynamic shared memory here
   if (pl.smemA > 48 * 1024 || pl.smemB > 48 * 1024 || pl.smemC > 48 * 1024)
     return bem::set_error(BEM_EINVAL, "bem_convolve_noalloc: grid too large for the default shared memory");
@@ -125,7 +133,15 @@ extern "C" int bem_convolve_noalloc(const double* khat, int Nx, int Ny, double c
   cudaStream_t s = (cudaStream_t)stream;
   unsigned char* scratch = static_cast<unsigned char*>(base);
   double* khat_t = reinterpret_cast<double*>(scratch + k_off);
+  double2* tw64 = reinterpret_cast<double2*>(scratch + t_off);
+  float2* tw32 = reinterpret_cast<float2*>(scratch + t32_off);
+  int* geo = reinterpret_cast<int*>(scratch + g_off);
+  bem::launch_geo_tables(geo, geo + bem::kSoEntries, pl.gA, 8, s);
+  bem::launch_geo_tables(geo + bem::kSoEntries + M, geo + 2 * bem::kSoEntries + M, pl.gB, 8, s);
   k_transpose_spectrum<<<dim3((hx + 127) / 128, hyq), 128, 0, s>>>(khat, khat_t, hx, hyq);
+  bem::launch_twiddles(tw64, tw32, ilog2i(M), s);
+  bem::launch_twiddles(tw64 + M, tw32 + M, ilog2i(py), s);
+  bem::launch_split_twiddles(tw64 + M + py, tw32 + M + py, M, s);
 
   bem::PassArgs<double> a{};
   a.pl = pl;
@@ -136,6 +152,13 @@ extern "C" int bem_convolve_noalloc(const double* khat, int Nx, int Ny, double c
   a.nrows_in = Ny;
   a.ncols_in = Nx;
   a.khat = khat_t;
+  a.twA = tw64;
+  a.twB = tw64 + M;
+  a.twS = tw64 + M + py;
+  a.soA = geo;
+  a.spA = geo + bem::kSoEntries;
+  a.soB = geo + bem::kSoEntries + M;
+  a.spB = geo + 2 * bem::kSoEntries + M;
   a.uscale = compliance / ((double)px * (double)py);
   bem::launch_pass_a<double>(a, bem::A_PLAIN, s);
   bem::launch_pass_b<double>(a, bem::B_CONV, s);

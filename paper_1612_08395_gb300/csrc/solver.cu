@@ -11,9 +11,25 @@
 
 #include "bem.h"
 #include "bem_impl.h"
+#include "geo_table.h"
 
 namespace bem {
-template <typename T> cudaError_t set_smem_attrs(int bytes);
+template <typename T> cudaError_t set_smem_attrs_a(int bytes);
+template <typename T> cudaError_t set_smem_attrs_b(int bytes);
+template <typename T> cudaError_t set_smem_attrs_c(int bytes);
+
+Geo make_geo(int logL, int rows, int esize) {
+  const GeoRow& r = (esize == 4 ? kGeo8 : kGeo16)[logL - 3];
+  int lr = 0;
+  while ((1 << lr) < rows) ++lr;
+  if (lr > 6) lr = 6;
+  Geo g{};
+  g.logL = logL;
+  g.r0 = logL % 3;
+  g.sa = r.a; g.sb = r.b; g.sc = r.c; g.sd = r.d;
+  g.rs = (1 << logL) + (rows > 1 ? r.pad[lr] : 0);
+  return g;
+}
 }
 
 using namespace bem;
@@ -49,6 +65,12 @@ namespace {
 
 constexpr int kChunk = 8;  // CG iterations per captured graph launch
 
+// Threads per CTA of the row passes (rows per CTA x M/8); 512 keeps two CTAs
+// resident per SM at the passes' register use.
+#ifndef BEM_MAX_THREADS_A
+#define BEM_MAX_THREADS_A 512
+#endif
+
 template <typename T> struct PrecFields {
   T *p = nullptr, *g = nullptr, *t = nullptr, *r = nullptr, *c = nullptr;
   bool ready = false;
@@ -61,27 +83,31 @@ int pow2_at_least(int v) { int p = 1; while (p < v) p <<= 1; return p; }
 Plan make_plan(int nx, int ny, int px, int py, int esize) {
   Plan pl{};
   pl.nx = nx; pl.ny = ny; pl.px = px; pl.py = py;
-  pl.M = px / 2; pl.logM = ilog2(pl.M); pl.logPy = ilog2(py);
+  pl.M = px / 2;
+  const int logM = ilog2(pl.M), logPy = ilog2(py);
   const int tr = pl.M / 8;
   int nb = 256 / tr;
-  const int sector = 32 / (2 * esize);
+  const int sector = 32 / (2 * esize);  // rows per CTA for 32-byte segments of W
   if (nb < sector) nb = sector;
   if (nb < 1) nb = 1;
-  while (nb > 1 && nb * tr > 1024) nb >>= 1;
-  while (nb > 1 && (size_t)nb * (pl.M + 1) * 2 * esize > 128 * 1024) nb >>= 1;
+  while (nb > 1 && nb * tr > BEM_MAX_THREADS_A) nb >>= 1;
+  while (nb > 1 && (size_t)nb * (pl.M + 32) * 2 * esize > 128 * 1024) nb >>= 1;
   pl.nbA = nb;
+  pl.lognbA = ilog2(nb);
+  pl.gA = make_geo(logM, nb, esize);
   pl.threadsA = nb * tr;
   pl.gridA = (ny + nb - 1) / nb;
-  pl.smemA = (size_t)nb * pl.M * 2 * esize;
-  pl.smemC = (size_t)nb * (pl.M + 1) * 2 * esize;
+  pl.smemA = (size_t)nb * pl.gA.rs * 2 * esize;
+  pl.smemC = pl.smemA;
   const int tb = py / 8;
   int nbb = 256 / tb;
   if (nbb < 1) nbb = 1;
-  while (nbb > 1 && (size_t)nbb * py * 2 * esize > 128 * 1024) nbb >>= 1;
+  while (nbb > 1 && (size_t)nbb * (py + 32) * 2 * esize > 128 * 1024) nbb >>= 1;
   pl.nbB = nbb;
+  pl.gB = make_geo(logPy, nbb, esize);
   pl.threadsB = nbb * tb;
-  pl.gridB = (pl.M + nbb - 1) / nbb;
-  pl.smemB = (size_t)nbb * py * 2 * esize;
+  pl.gridB = (pl.M + 1 + nbb - 1) / nbb;
+  pl.smemB = (size_t)nbb * pl.gB.rs * 2 * esize;
   return pl;
 }
 
@@ -94,6 +120,9 @@ struct bem_ctx {
   int nx = 0, ny = 0, px = 0, py = 0;
   double dx = 0, dy = 0, k = 0, nu = 0, E0 = 0, c0 = 0, alpha = 0, A = 0;
   double* kq64 = nullptr;
+  int* geo = nullptr;       // index tables: [A32 | B32 | A64 | B64], each so (112) + sp (L)
+  double2* tw64 = nullptr;  // [length-M stages | length-Py stages | split], FP64
+  float2* tw32 = nullptr;   // the same, FP32
   double* khat64 = nullptr;
   float* khat32 = nullptr;
   void* W = nullptr;
@@ -171,6 +200,17 @@ PassArgs<T> make_args(bem_ctx* h) {
   a.nrows_in = h->ny;
   a.ncols_in = h->nx;
   a.khat = khat_of<T>(h);
+  const size_t M = h->px / 2, P = h->py;
+  if constexpr (sizeof(T) == 8) {
+    a.twA = h->tw64; a.twB = h->tw64 + M; a.twS = h->tw64 + M + P;
+  } else {
+    a.twA = h->tw32; a.twB = h->tw32 + M; a.twS = h->tw32 + M + P;
+  }
+  const int* gt = h->geo + (sizeof(T) == 8 ? 2 * kSoEntries + M + P : 0);
+  a.soA = gt;
+  a.spA = gt + kSoEntries;
+  a.soB = gt + kSoEntries + M;
+  a.spB = gt + 2 * kSoEntries + M;
   a.uscale = h->A / ((double)h->px * (double)h->py);
   a.partA = h->part;
   a.partC = h->partC;
@@ -492,8 +532,12 @@ extern "C" int bem_create(int Nx, int Ny, double dx, double dy, double k, double
   if (!attrs_done) {
     // plans never ask for more than 128 KB + one row of dynamic shared memory
     const int smem_max = 136 * 1024;
-    cudaError_t ea = set_smem_attrs<float>(smem_max);
-    if (ea == cudaSuccess) ea = set_smem_attrs<double>(smem_max);
+    cudaError_t ea = set_smem_attrs_a<float>(smem_max);
+    if (ea == cudaSuccess) ea = set_smem_attrs_b<float>(smem_max);
+    if (ea == cudaSuccess) ea = set_smem_attrs_c<float>(smem_max);
+    if (ea == cudaSuccess) ea = set_smem_attrs_a<double>(smem_max);
+    if (ea == cudaSuccess) ea = set_smem_attrs_b<double>(smem_max);
+    if (ea == cudaSuccess) ea = set_smem_attrs_c<double>(smem_max);
     if (ea != cudaSuccess)
       return cleanup(fail(BEM_ECUDA, "shared-memory opt-in failed: %s", cudaGetErrorString(ea)));
     if (influence_init_nodes() != 0) return cleanup(fail(BEM_ECUDA, "quadrature nodes upload failed"));
@@ -502,14 +546,18 @@ extern "C" int bem_create(int Nx, int Ny, double dx, double dy, double k, double
   h->nx = Nx; h->ny = Ny; h->dx = dx; h->dy = dy; h->k = k; h->nu = nu; h->E0 = E0; h->c0 = c0;
   h->alpha = alpha;
   h->A = alpha * (1.0 - nu * nu) * pow(c0, k) / E0;  // Eq. 12
-  h->px = pow2_at_least(2 * Nx < 16 ? 16 : 2 * Nx);
-  h->py = pow2_at_least(2 * Ny < 16 ? 16 : 2 * Ny);
+  h->px = pow2_at_least(2 * Nx < 32 ? 32 : 2 * Nx);
+  h->py = pow2_at_least(2 * Ny < 32 ? 32 : 2 * Ny);
   h->plan32 = make_plan(Nx, Ny, h->px, h->py, 4);
   h->plan64 = make_plan(Nx, Ny, h->px, h->py, 8);
   const int M = h->px / 2, hyq = h->py / 2 + 1;
   const size_t n = (size_t)Nx * Ny;
   int rc;
   if ((rc = dmalloc(h, (void**)&h->kq64, sizeof(double) * (size_t)hyq * (M + 1)))) return cleanup(rc);
+  const size_t ntw = (size_t)M + h->py + M + 1;
+  if ((rc = dmalloc(h, (void**)&h->tw64, sizeof(double2) * ntw))) return cleanup(rc);
+  if ((rc = dmalloc(h, (void**)&h->tw32, sizeof(float2) * ntw))) return cleanup(rc);
+  if ((rc = dmalloc(h, (void**)&h->geo, sizeof(int) * 2 * (2 * kSoEntries + M + h->py)))) return cleanup(rc);
   if ((rc = dmalloc(h, (void**)&h->khat64, sizeof(double) * (size_t)hyq * (M + 1)))) return cleanup(rc);
   if ((rc = dmalloc(h, (void**)&h->khat32, sizeof(float) * (size_t)hyq * (M + 1)))) return cleanup(rc);
   if ((rc = dmalloc(h, &h->W, sizeof(double) * 2 * (size_t)(M + 1) * Ny))) return cleanup(rc);
@@ -534,6 +582,17 @@ extern "C" int bem_create(int Nx, int Ny, double dx, double dy, double k, double
       cudaMemsetAsync(h->S, 0, n, h->stream) != cudaSuccess)
     return cleanup(fail(BEM_ECUDA, "memset failed"));
 
+  {
+    int* g32 = h->geo;
+    int* g64 = h->geo + 2 * kSoEntries + M + h->py;
+    launch_geo_tables(g32, g32 + kSoEntries, h->plan32.gA, 4, h->stream);
+    launch_geo_tables(g32 + kSoEntries + M, g32 + 2 * kSoEntries + M, h->plan32.gB, 4, h->stream);
+    launch_geo_tables(g64, g64 + kSoEntries, h->plan64.gA, 8, h->stream);
+    launch_geo_tables(g64 + kSoEntries + M, g64 + 2 * kSoEntries + M, h->plan64.gB, 8, h->stream);
+  }
+  launch_twiddles(h->tw64, h->tw32, ilog2(M), h->stream);
+  launch_twiddles(h->tw64 + M, h->tw32 + M, ilog2(h->py), h->stream);
+  launch_split_twiddles(h->tw64 + M + h->py, h->tw32 + M + h->py, M, h->stream);
   // a1: influence coefficients on the offsets 0..Px/2, 0..Py/2 (Eq. 9)
   launch_influence(h->kq64, M + 1, hyq, dx, dy, k, h->stream);
   // spectrum of the even torus extension (Eq. 13: FFT(K)), FP64, once
@@ -543,6 +602,10 @@ extern "C" int bem_create(int Nx, int Ny, double dx, double dy, double k, double
       return cleanup(fail(BEM_ENOMEM, "spectrum workspace allocation failed"));
     PassArgs<double> a{};
     a.pl = h->plan64;
+    a.twA = h->tw64; a.twB = h->tw64 + M; a.twS = h->tw64 + M + h->py;
+    const int* g64 = h->geo + 2 * kSoEntries + M + h->py;
+    a.soA = g64; a.spA = g64 + kSoEntries;
+    a.soB = g64 + kSoEntries + M; a.spB = g64 + 2 * kSoEntries + M;
     a.W = Wspec;
     a.rows_w = h->py;
     a.nrows_in = h->py;
@@ -572,7 +635,7 @@ extern "C" void bem_destroy(bem_handle h) {
   for (int i = 0; i < 2; ++i)
     for (int j = 0; j < 4; ++j)
       if (h->ev[i][j]) cudaEventDestroy(h->ev[i][j]);
-  fr(h->kq64); fr(h->khat64); fr(h->khat32); fr(h->W); fr(h->h64); fr(h->io64); fr(h->io64b);
+  fr(h->kq64); fr(h->geo); fr(h->tw64); fr(h->tw32); fr(h->khat64); fr(h->khat32); fr(h->W); fr(h->h64); fr(h->io64); fr(h->io64b);
   fr(h->S); fr(h->part); fr(h->partC); fr(h->partE); fr(h->stats); fr(h->sc);
   fr(h->f32.p); fr(h->f32.g); fr(h->f32.t); fr(h->f32.r); fr(h->f32.c);
   fr(h->f64.p); fr(h->f64.g); fr(h->f64.t); fr(h->f64.r); fr(h->f64.c);

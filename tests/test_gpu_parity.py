@@ -20,8 +20,8 @@ def relL2(a, b):
 
 
 def torus_sizes(nx, ny):
-    px = max(16, 1 << int(math.ceil(math.log2(2 * nx))))
-    py = max(16, 1 << int(math.ceil(math.log2(2 * ny))))
+    px = max(32, 1 << int(math.ceil(math.log2(2 * nx))))
+    py = max(32, 1 << int(math.ceil(math.log2(2 * ny))))
     return px, py
 
 
