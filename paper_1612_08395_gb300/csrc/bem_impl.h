@@ -38,6 +38,7 @@ struct Plan {
   int gridB;  // = ceil((M + 1) / nbB)
   int threadsA, threadsB;
   size_t smemA, smemB, smemC;
+  int nsm;    // SMs of the device (persistent launches size their grids by it)
 };
 
 // Device-resident scalar state of one CG solve (FP64 throughout).
@@ -46,6 +47,7 @@ struct Scalars {
   double tau, beta, delta, G, G_old, eps, bnorm, pcrit;
   double sum_p, sum_dp, n_ol, n_ic, str, eps_min;
   int max_iter, iter, done, status, have_tau, it_min;
+  int nA, pad1;   // CTAs of the last pass A launch (its partials feed pass C)
   unsigned int cnt_a, cnt_c, cnt_e, cnt_r;  // last-block arrival counters
 };
 

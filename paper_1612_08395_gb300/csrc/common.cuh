@@ -172,6 +172,26 @@ __device__ __forceinline__ void dit8(C<T>* buf, int t, int ls, const C<T>* tw, c
 }
 
 // ---------------------------------------------------------------------------
+// Asynchronous global -> shared copies (16-byte chunks, L2 only).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+template <typename Cx>
+__device__ __forceinline__ void cp_async_cx(Cx* smem, const Cx* gmem) {
+  if (sizeof(Cx) == 16) cp_async16(smem, gmem);
+  else cp_async8(smem, gmem);
+}
+
+// ---------------------------------------------------------------------------
 // FP64 block reduction of NQ values; result valid in thread 0.  `red` must hold
 // NQ * (blockDim.x/32) doubles of shared memory.
 template <int NQ>

@@ -26,6 +26,11 @@
 // `done` flag is set, so a captured chunk of iterations can run past
 // convergence at the cost of empty launches.
 #pragma once
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "bem_impl.h"
 #include "common.cuh"
 #include "geo_table.h"
@@ -211,10 +216,18 @@ __device__ __forceinline__ T pro_apply(const PassArgs<T>& a, size_t i, const PIn
   }
 }
 
+// Launch bounds of the row passes (A and C): the plan caps their CTAs at
+// BEM_MAX_THREADS_A threads except for the longest rows; three resident CTAs
+// per SM (registers capped accordingly) hide more of the global latency.
+#ifndef BEM_ROW_MIN_BLOCKS
+#define BEM_ROW_MIN_BLOCKS 3
+#endif
+#define BEM_ROW_BOUNDS(LOGL) __launch_bounds__((LOGL) >= 13 ? 1024 : 512, (LOGL) >= 13 ? 1 : BEM_ROW_MIN_BLOCKS)
+
 // ---------------------------------------------------------------------------
 // Pass A: nbA rows per CTA, M/8 threads per row.
 template <typename T, int MODE, int LOGL>
-__global__ void __launch_bounds__(1024) k_pass_a(PassArgs<T> a) {
+__global__ void BEM_ROW_BOUNDS(LOGL) k_pass_a(PassArgs<T> a) {
   using Cx = C<T>;
   using F = FftC<T, LOGL>;
   constexpr int L = F::L, L8 = F::L8, M = L;
@@ -241,6 +254,7 @@ __global__ void __launch_bounds__(1024) k_pass_a(PassArgs<T> a) {
   T tau = 0, beta = 0;
   if (MODE == A_PK_P) { upd = sc->have_tau != 0; tau = (T)sc->tau; }
   if (MODE == A_PK_T || MODE == A_CG_T) beta = (T)sc->beta;
+  if (MODE == A_PK_P && blockIdx.x == 0 && tid == 0) sc->nA = gridDim.x;
   const size_t rowoff = (size_t)row * ncols;
 
   Cx v[8];
@@ -327,9 +341,174 @@ __global__ void __launch_bounds__(1024) k_pass_a(PassArgs<T> a) {
 }
 
 // ---------------------------------------------------------------------------
-// Pass B: nbB columns per CTA, Py/8 threads per column; columns kx = 0..M.
+// Persistent pass A: each CTA loops over row groups (nbA rows each) and, while
+// it transforms one group, its prologue fields for the next group stream into
+// shared memory with cp.async.  Used when rows are multiples of 16 elements.
+template <int MODE> struct ProStage {
+  static constexpr int nT = (MODE == A_PK_P || MODE == A_PK_T) ? 3 : (MODE == A_CG_T ? 2 : (MODE == A_PLAIN ? 1 : 0));
+  static constexpr bool S = MODE == A_CG_T;
+};
+template <typename T, int MODE>
+__host__ __device__ constexpr size_t pro_stage_bytes(int nb, int nx) {
+  return ((size_t)ProStage<MODE>::nT * sizeof(T) + (ProStage<MODE>::S ? 1 : 0)) * (size_t)nb * nx;
+}
+template <typename T, int MODE>
+__device__ __forceinline__ const T* pro_field(const PassArgs<T>& a, int f) {
+  if (MODE == A_PLAIN) return a.f.src;
+  if (MODE == A_CG_T) return f == 0 ? a.f.t : a.f.g;
+  return f == 0 ? a.f.p : (f == 1 ? a.f.t : a.f.g);
+}
+template <typename T, int MODE>
+__device__ __forceinline__ void pro_prefetch(const PassArgs<T>& a, T* st, uint8_t* ss, int row0, int rows,
+                                             int nx, int nb) {
+  const int cpr = nx * (int)sizeof(T) / 16;
+#pragma unroll
+  for (int f = 0; f < ProStage<MODE>::nT; ++f) {
+    const T* src = pro_field<T, MODE>(a, f);
+    for (int q = threadIdx.x; q < cpr * rows; q += blockDim.x) {
+      const int bb = q / cpr, ch = q - bb * cpr;
+      cp_async16(reinterpret_cast<char*>(st + ((size_t)f * nb + bb) * nx) + 16 * ch,
+                 reinterpret_cast<const char*>(src + (size_t)(row0 + bb) * nx) + 16 * ch);
+    }
+  }
+  if (ProStage<MODE>::S) {
+    const int cps = nx / 16;
+    for (int q = threadIdx.x; q < cps * rows; q += blockDim.x) {
+      const int bb = q / cps, ch = q - bb * cps;
+      cp_async16(ss + (size_t)bb * nx + 16 * ch, a.f.S + (size_t)(row0 + bb) * nx + 16 * ch);
+    }
+  }
+  cp_async_commit();
+}
+template <typename T, int MODE>
+__device__ __forceinline__ void pro_gather_staged(const T* st, const uint8_t* ss, int b, int col, int nx,
+                                                  int nb, PIn<T>& x) {
+  const size_t j = (size_t)b * nx + col, plane = (size_t)nb * nx;
+  if (MODE == A_PLAIN) { x.p = st[j]; }
+  else if (MODE == A_CG_T) { x.t = st[j]; x.g = st[plane + j]; x.s = ss[j]; }
+  else { x.p = st[j]; x.t = st[plane + j]; x.g = st[2 * plane + j]; }
+}
+
+#ifndef BEM_ROWP_MIN_BLOCKS
+#define BEM_ROWP_MIN_BLOCKS 2
+#endif
+#define BEM_ROWP_BOUNDS(LOGL) __launch_bounds__((LOGL) >= 13 ? 1024 : 512, (LOGL) >= 13 ? 1 : BEM_ROWP_MIN_BLOCKS)
+
 template <typename T, int MODE, int LOGL>
-__global__ void __launch_bounds__(1024) k_pass_b(PassArgs<T> a) {
+__global__ void BEM_ROWP_BOUNDS(LOGL) k_pass_ap(PassArgs<T> a) {
+  using Cx = C<T>;
+  using F = FftC<T, LOGL>;
+  constexpr int L = F::L, L8 = F::L8, M = L;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[3 * 32];
+  Cx* sm = reinterpret_cast<Cx*>(smem_raw);
+  Scalars* sc = a.sc;
+  if (MODE != A_PLAIN) {
+    if (sc->done) return;
+  }
+  const int nb = a.pl.nbA, lognb = a.pl.lognbA, rs = a.pl.gA.rs;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int b = tid >> (LOGL - 3), t = tid & (L8 - 1);
+  const int ncols = a.ncols_in, nrows = a.nrows_in;
+  const int half = (ncols + 1) >> 1;
+  const int G = (nrows + nb - 1) / nb;
+  Cx* buf = sm + b * rs;
+  T* st = reinterpret_cast<T*>(smem_raw + ((sizeof(Cx) * (size_t)nb * rs + 15) & ~(size_t)15));
+  uint8_t* ss = reinterpret_cast<uint8_t*>(st) + (size_t)ProStage<MODE>::nT * sizeof(T) * nb * ncols;
+  const Cx* tw = reinterpret_cast<const Cx*>(a.twA);
+  const Cx* tws = reinterpret_cast<const Cx*>(a.twS);
+  const int* sp = a.spA;
+  Cx* W = reinterpret_cast<Cx*>(a.W);
+  T acc[3] = {0, 0, 0};
+  bool upd = false;
+  T tau = 0, beta = 0;
+  if (MODE == A_PK_P) { upd = sc->have_tau != 0; tau = (T)sc->tau; }
+  if (MODE == A_PK_T || MODE == A_CG_T) beta = (T)sc->beta;
+  if (MODE == A_PK_P && blockIdx.x == 0 && tid == 0) sc->nA = gridDim.x;
+
+  int g = blockIdx.x;
+  if (g < G) pro_prefetch<T, MODE>(a, st, ss, g * nb, min(nb, nrows - g * nb), ncols, nb);
+  for (; g < G; g += gridDim.x) {
+    const int row0 = g * nb, row = row0 + b;
+    const bool act = row < nrows;
+    const size_t rowoff = (size_t)row * ncols;
+    cp_async_wait_all();
+    __syncthreads();
+    PIn<T> in[8][2];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      if (!F::first_half(e)) continue;
+      const int n = F::n0(t, e);
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        if (act && n < half && 2 * n + h < ncols)
+          pro_gather_staged<T, MODE>(st, ss, b, 2 * n + h, ncols, nb, in[e][h]);
+    }
+    __syncthreads();  // staging consumed: refill it for the next group
+    const int gn = g + gridDim.x;
+    if (gn < G) pro_prefetch<T, MODE>(a, st, ss, gn * nb, min(nb, nrows - gn * nb), ncols, nb);
+    Cx v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      v[e] = mk<T>(0, 0);
+      if (!F::first_half(e)) continue;
+      const int n = F::n0(t, e);
+      T xv[2] = {0, 0};
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        if (act && n < half && 2 * n + h < ncols)
+          xv[h] = pro_apply<T, MODE>(a, rowoff + 2 * n + h, in[e][h], upd, tau, beta, acc);
+      v[e] = mk<T>(xv[0], xv[1]);
+    }
+    F::stage0_fwd(v, t, tw);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) buf[F::ix0(t, e)] = v[e];
+    __syncthreads();
+#pragma unroll
+    for (int ls = F::LS_TOP; ls >= 0; ls -= 3) {
+      F::dif(buf, t, ls, tw);
+      __syncthreads();
+    }
+#pragma unroll 3
+    for (int idx = tid; idx < (M + 1) << lognb; idx += nthr) {
+      const int k = idx >> lognb, bb = idx & (nb - 1);
+      const int rw = row0 + bb;
+      if (rw >= nrows) continue;
+      const Cx* s = sm + bb * rs;
+      Cx X;
+      if (k == 0 || k == M) {
+        const Cx z0 = s[0];
+        X = mk<T>(k == 0 ? z0.x + z0.y : z0.x - z0.y, (T)0);
+      } else {
+        const Cx zk = s[__ldg(sp + k)];
+        const Cx zm = conj<T>(s[__ldg(sp + M - k)]);
+        const Cx E = scale<T>(add<T>(zk, zm), (T)0.5);
+        const Cx dlt = sub<T>(zk, zm);
+        const Cx O = mk<T>((T)0.5 * dlt.y, (T)-0.5 * dlt.x);
+        X = add<T>(E, mul<T>(__ldg(tws + k), O));
+      }
+      W[(size_t)k * a.rows_w + rw] = X;
+    }
+  }
+  cp_async_wait_all();
+  if (MODE == A_PK_P) {
+    double vv[3] = {(double)acc[0], (double)acc[1], (double)acc[2]};
+    block_sum<3>(vv, red);
+    if (tid == 0) {
+      double* pp = a.partA + 4 * blockIdx.x;
+      pp[0] = vv[0]; pp[1] = vv[1]; pp[2] = vv[2];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pass B: nbB columns per CTA, Py/8 threads per column; columns kx = 0..M.
+#ifndef BEM_COL_MIN_BLOCKS
+#define BEM_COL_MIN_BLOCKS 3
+#endif
+template <typename T, int MODE, int LOGL>
+__global__ void __launch_bounds__((LOGL) >= 13 ? 1024 : 512, (LOGL) >= 13 ? 1 : BEM_COL_MIN_BLOCKS)
+    k_pass_b(PassArgs<T> a) {
   using Cx = C<T>;
   using F = FftC<T, LOGL>;
   constexpr int L = F::L, L8 = F::L8, R0 = F::R0, hyq = (L >> 1) + 1;
@@ -420,6 +599,20 @@ __global__ void __launch_bounds__(1024) k_pass_b(PassArgs<T> a) {
   (void)R0;
 }
 
+// Epilogue fields of pass C that are prefetched into shared memory at kernel
+// start (their loads then overlap the inverse transform): number of T-typed
+// fields and whether the contact set S (one byte per element) is staged.
+template <int MODE> struct EpiStage {
+  static constexpr int nT = MODE == C_PK_G ? 2 : (MODE == C_CG_R || MODE == C_CG_G || MODE == C_GAP) ? 1 : 0;
+  static constexpr bool S = MODE == C_CG_R || MODE == C_CG_G;
+  static constexpr bool any = nT > 0 || S;
+};
+// Bytes of that staging area for nb rows of nx elements.
+template <typename T, int MODE>
+__host__ __device__ constexpr size_t epi_stage_bytes(int nb, int nx) {
+  return ((size_t)EpiStage<MODE>::nT * sizeof(T) + (EpiStage<MODE>::S ? 1 : 0)) * (size_t)nb * nx;
+}
+
 // ---------------------------------------------------------------------------
 // Pass C epilogue, in two phases like the prologue.
 template <typename T>
@@ -441,6 +634,17 @@ __device__ __forceinline__ void epi_gather(const PassArgs<T>& a, size_t i, EIn<T
   } else if (MODE == C_GAP) {
     x.c = a.f.c[i];
   }
+}
+
+// Gather from the shared-memory staging area: T fields [f][b][col], then S [b][col].
+template <typename T, int MODE>
+__device__ __forceinline__ void epi_gather_staged(const T* st, const uint8_t* ss, int b, int col, int nx,
+                                                  int nb, EIn<T>& x) {
+  const size_t j = (size_t)b * nx + col, plane = (size_t)nb * nx;
+  if (MODE == C_PK_G) { x.c = st[j]; x.p = st[plane + j]; }
+  else if (MODE == C_CG_R) { x.t = st[j]; x.s = ss[j]; }
+  else if (MODE == C_CG_G) { x.c = st[j]; x.s = ss[j]; }
+  else if (MODE == C_GAP) { x.c = st[j]; }
 }
 
 template <typename T, int MODE>
@@ -471,121 +675,11 @@ __device__ __forceinline__ void epi_apply(const PassArgs<T>& a, size_t i, T u, c
   }
 }
 
-template <typename T, int MODE, int LOGL>
-__global__ void __launch_bounds__(1024) k_pass_c(PassArgs<T> a) {
-  using Cx = C<T>;
-  using F = FftC<T, LOGL>;
-  constexpr int L = F::L, L8 = F::L8, M = L;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[3 * 32];
-  __shared__ int lastflag;
-  Cx* sm = reinterpret_cast<Cx*>(smem_raw);
-  Scalars* sc = a.sc;
-  if (MODE != C_PLAIN && MODE != C_GAP) {
-    if (sc->done) return;
-  }
-  const int nb = a.pl.nbA, lognb = a.pl.lognbA, rs = a.pl.gA.rs;
-  const int nx = a.pl.nx, ny = a.pl.ny;
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  const int b = tid >> (LOGL - 3), t = tid & (L8 - 1);
-  const int row0 = blockIdx.x * nb;
-  const Cx* W = reinterpret_cast<const Cx*>(a.W);
-  const Cx* tws = reinterpret_cast<const Cx*>(a.twS);
-  const Cx* tw = reinterpret_cast<const Cx*>(a.twA);
-  const int* sp = a.spA;
-  // rebuild the packed half-length spectrum, scattered to digit-reversed
-  // positions: Z[k] = E + i O, E = X[k] + conj X[M-k], O = (X[k] - conj X[M-k]) e^{+i pi k/M}.
-  // Each thread handles up to NP pairs (k, M-k); all loads are issued first.
-  {
-    constexpr int hm = (M >> 1) + 1;
-    const int total = hm << lognb;
-    constexpr int NP = 5;  // ceil((M/2 + 1) nb / (nb M/8)) for M >= 16
-    Cx xk[NP], xm[NP];
-#pragma unroll
-    for (int j = 0; j < NP; ++j) {
-      const int idx = tid + j * nthr;
-      xk[j] = mk<T>(0, 0);
-      xm[j] = mk<T>(0, 0);
-      if (idx < total) {
-        const int k = idx >> lognb, rw = row0 + (idx & (nb - 1));
-        if (rw < ny) {
-          xk[j] = W[(size_t)k * a.rows_w + rw];
-          xm[j] = W[(size_t)(M - k) * a.rows_w + rw];
-        }
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < NP; ++j) {
-      const int idx = tid + j * nthr;
-      if (idx >= total) continue;
-      const int k = idx >> lognb, bb = idx & (nb - 1);
-      Cx* s = sm + bb * rs;
-      const Cx wk = conj<T>(__ldg(tws + k));
-      {
-        const Cx E = add<T>(xk[j], conj<T>(xm[j]));
-        const Cx O = mul<T>(sub<T>(xk[j], conj<T>(xm[j])), wk);
-        s[__ldg(sp + k)] = add<T>(E, mul_si<T, 1>(O));
-      }
-      if (k != 0 && k != M - k) {
-        const Cx wm = mk<T>(-wk.x, wk.y);  // exp(+i pi (M-k)/M) = -conj(wk)
-        const Cx E = add<T>(xm[j], conj<T>(xk[j]));
-        const Cx O = mul<T>(sub<T>(xm[j], conj<T>(xk[j])), wm);
-        s[__ldg(sp + M - k)] = add<T>(E, mul_si<T, 1>(O));
-      }
-    }
-  }
-  __syncthreads();
-  Cx* buf = sm + b * rs;
-#pragma unroll
-  for (int ls = 0; ls <= F::LS_TOP; ls += 3) {
-    F::dit(buf, t, ls, tw);
-    __syncthreads();
-  }
-  // last DIT stage: natural-order outputs z[n] = (x[2n], x[2n+1]) * Px; the
-  // epilogue fields are gathered first so their loads overlap the stage
-  const T us = (T)a.uscale;
-  T acc[3] = {0, 0, 0};
-  const int row = row0 + b;
-  const bool act = row < ny;
-  const size_t rowoff = (size_t)row * nx;
-  const int half = (nx + 1) >> 1;
-  EIn<T> ein[8][2];
-  if (MODE != C_PLAIN) {
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      if (!F::first_half(e)) continue;
-      const int n = F::n0(t, e);
-#pragma unroll
-      for (int h = 0; h < 2; ++h)
-        if (act && n < half && 2 * n + h < nx) epi_gather<T, MODE>(a, rowoff + 2 * n + h, ein[e][h]);
-    }
-  }
-  Cx v[8];
-#pragma unroll
-  for (int e = 0; e < 8; ++e) v[e] = buf[F::ix0(t, e)];
-  F::stage0_inv(v, t, tw);
-#pragma unroll
-  for (int e = 0; e < 8; ++e) {
-    if (!F::first_half(e)) continue;
-    const int n = F::n0(t, e);
-#pragma unroll
-    for (int h = 0; h < 2; ++h)
-      if (act && n < half && 2 * n + h < nx)
-        epi_apply<T, MODE>(a, rowoff + 2 * n + h, us * (h ? v[e].y : v[e].x), ein[e][h], acc);
-  }
-  if (MODE == C_PLAIN || MODE == C_GAP) return;
-  double vv[2] = {(double)acc[0], (double)acc[1]};
-  block_sum<2>(vv, red);
-  if (tid == 0) {
-    double* pp = a.partC + 4 * blockIdx.x;
-    pp[0] = vv[0]; pp[1] = vv[1];
-  }
-  if (!last_block_arrival(MODE == C_PK_G ? &sc->cnt_c : &sc->cnt_a, &lastflag)) return;
-  double s2[2];
-  sum_partials<2>(a.partC, gridDim.x, s2, red);
-  double s3[3] = {0, 0, 0};
-  if (MODE == C_PK_G) sum_partials<3>(a.partA, gridDim.x, s3, red);
-  if (tid != 0) return;
+// Scalar work of the last CTA of a pass-C launch (FP64): the Polonsky-Keer
+// stopping test and beta after the gap pass, tau after the r pass, tau or the
+// initial residual of the fixed-set CG.
+template <int MODE>
+__device__ __forceinline__ void pass_c_finalize(Scalars* sc, const double (&s2)[2], const double (&s3)[3]) {
   if (MODE == C_PK_G) {
     sc->cnt_c = 0;
     const double G = s2[0], nic = s2[1];
@@ -648,6 +742,315 @@ __global__ void __launch_bounds__(1024) k_pass_c(PassArgs<T> a) {
   }
 }
 
+template <typename T, int MODE, int LOGL>
+__global__ void BEM_ROW_BOUNDS(LOGL) k_pass_c(PassArgs<T> a) {
+  using Cx = C<T>;
+  using F = FftC<T, LOGL>;
+  constexpr int L = F::L, L8 = F::L8, M = L;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[3 * 32];
+  __shared__ int lastflag;
+  Cx* sm = reinterpret_cast<Cx*>(smem_raw);
+  Scalars* sc = a.sc;
+  if (MODE != C_PLAIN && MODE != C_GAP) {
+    if (sc->done) return;
+  }
+  const int nb = a.pl.nbA, lognb = a.pl.lognbA, rs = a.pl.gA.rs;
+  const int nx = a.pl.nx, ny = a.pl.ny;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int b = tid >> (LOGL - 3), t = tid & (L8 - 1);
+  const int row0 = blockIdx.x * nb;
+  const Cx* W = reinterpret_cast<const Cx*>(a.W);
+  const Cx* tws = reinterpret_cast<const Cx*>(a.twS);
+  const Cx* tw = reinterpret_cast<const Cx*>(a.twA);
+  const int* sp = a.spA;
+  // prefetch the epilogue fields of this CTA's rows (if rows are 16-byte multiples)
+  constexpr bool kStage = EpiStage<MODE>::any;
+  const bool staged = kStage && (nx & 15) == 0 && row0 + nb <= ny;
+  T* st = reinterpret_cast<T*>(smem_raw + ((sizeof(Cx) * (size_t)nb * rs + 15) & ~(size_t)15));
+  uint8_t* ss = reinterpret_cast<uint8_t*>(st) + (size_t)EpiStage<MODE>::nT * sizeof(T) * nb * nx;
+  if (staged) {
+    const int cpr = nx * (int)sizeof(T) / 16;  // 16-byte chunks per row of a T field
+#pragma unroll
+    for (int f = 0; f < EpiStage<MODE>::nT; ++f) {
+      const T* src = (MODE == C_PK_G) ? (f == 0 ? a.f.c : a.f.p) : (MODE == C_CG_R ? a.f.t : a.f.c);
+      for (int q = tid; q < cpr * nb; q += nthr) {
+        const int bb = q / cpr, ch = q - bb * cpr;
+        cp_async16(reinterpret_cast<char*>(st + ((size_t)f * nb + bb) * nx) + 16 * ch,
+                   reinterpret_cast<const char*>(src + (size_t)(row0 + bb) * nx) + 16 * ch);
+      }
+    }
+    if (EpiStage<MODE>::S) {
+      const int cps = nx / 16;
+      for (int q = tid; q < cps * nb; q += nthr) {
+        const int bb = q / cps, ch = q - bb * cps;
+        cp_async16(ss + (size_t)bb * nx + 16 * ch, a.f.S + (size_t)(row0 + bb) * nx + 16 * ch);
+      }
+    }
+    cp_async_commit();
+  }
+  // rebuild the packed half-length spectrum, scattered to digit-reversed
+  // positions: Z[k] = E + i O, E = X[k] + conj X[M-k], O = (X[k] - conj X[M-k]) e^{+i pi k/M}.
+  // Each thread handles up to NP pairs (k, M-k); all loads are issued first.
+  {
+    constexpr int hm = (M >> 1) + 1;
+    const int total = hm << lognb;
+    constexpr int NP = 5;  // ceil((M/2 + 1) nb / (nb M/8)) for M >= 16
+    Cx xk[NP], xm[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      const int idx = tid + j * nthr;
+      xk[j] = mk<T>(0, 0);
+      xm[j] = mk<T>(0, 0);
+      if (idx < total) {
+        const int k = idx >> lognb, rw = row0 + (idx & (nb - 1));
+        if (rw < ny) {
+          xk[j] = W[(size_t)k * a.rows_w + rw];
+          xm[j] = W[(size_t)(M - k) * a.rows_w + rw];
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      const int idx = tid + j * nthr;
+      if (idx >= total) continue;
+      const int k = idx >> lognb, bb = idx & (nb - 1);
+      Cx* s = sm + bb * rs;
+      const Cx wk = conj<T>(__ldg(tws + k));
+      {
+        const Cx E = add<T>(xk[j], conj<T>(xm[j]));
+        const Cx O = mul<T>(sub<T>(xk[j], conj<T>(xm[j])), wk);
+        s[__ldg(sp + k)] = add<T>(E, mul_si<T, 1>(O));
+      }
+      if (k != 0 && k != M - k) {
+        const Cx wm = mk<T>(-wk.x, wk.y);  // exp(+i pi (M-k)/M) = -conj(wk)
+        const Cx E = add<T>(xm[j], conj<T>(xk[j]));
+        const Cx O = mul<T>(sub<T>(xm[j], conj<T>(xk[j])), wm);
+        s[__ldg(sp + M - k)] = add<T>(E, mul_si<T, 1>(O));
+      }
+    }
+  }
+  __syncthreads();
+  Cx* buf = sm + b * rs;
+#pragma unroll
+  for (int ls = 0; ls <= F::LS_TOP; ls += 3) {
+    F::dit(buf, t, ls, tw);
+    __syncthreads();
+  }
+  // last DIT stage: natural-order outputs z[n] = (x[2n], x[2n+1]) * Px; the
+  // epilogue fields are gathered first so their loads overlap the stage
+  const T us = (T)a.uscale;
+  T acc[3] = {0, 0, 0};
+  const int row = row0 + b;
+  const bool act = row < ny;
+  const size_t rowoff = (size_t)row * nx;
+  const int half = (nx + 1) >> 1;
+  EIn<T> ein[8][2];
+  if (staged) {
+    cp_async_wait_all();
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      if (!F::first_half(e)) continue;
+      const int n = F::n0(t, e);
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        if (act && n < half && 2 * n + h < nx)
+          epi_gather_staged<T, MODE>(st, ss, b, 2 * n + h, nx, nb, ein[e][h]);
+    }
+  } else if (MODE != C_PLAIN) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      if (!F::first_half(e)) continue;
+      const int n = F::n0(t, e);
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        if (act && n < half && 2 * n + h < nx) epi_gather<T, MODE>(a, rowoff + 2 * n + h, ein[e][h]);
+    }
+  }
+  Cx v[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) v[e] = buf[F::ix0(t, e)];
+  F::stage0_inv(v, t, tw);
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    if (!F::first_half(e)) continue;
+    const int n = F::n0(t, e);
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+      if (act && n < half && 2 * n + h < nx)
+        epi_apply<T, MODE>(a, rowoff + 2 * n + h, us * (h ? v[e].y : v[e].x), ein[e][h], acc);
+  }
+  if (MODE == C_PLAIN || MODE == C_GAP) return;
+  double vv[2] = {(double)acc[0], (double)acc[1]};
+  block_sum<2>(vv, red);
+  if (tid == 0) {
+    double* pp = a.partC + 4 * blockIdx.x;
+    pp[0] = vv[0]; pp[1] = vv[1];
+  }
+  if (!last_block_arrival(MODE == C_PK_G ? &sc->cnt_c : &sc->cnt_a, &lastflag)) return;
+  double s2[2];
+  sum_partials<2>(a.partC, gridDim.x, s2, red);
+  double s3[3] = {0, 0, 0};
+  if (MODE == C_PK_G) sum_partials<3>(a.partA, __ldcg(&sc->nA), s3, red);
+  if (tid != 0) return;
+  pass_c_finalize<MODE>(sc, s2, s3);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent pass C: each CTA loops over row groups; the strided W rows of the
+// next group and the epilogue fields stream into shared memory with cp.async
+// (two commit groups per row group, waited for separately) while the current
+// group is transformed.  Used when rows are multiples of 16 elements.
+template <typename T, int MODE, int LOGL>
+__global__ void BEM_ROWP_BOUNDS(LOGL) k_pass_cp(PassArgs<T> a) {
+  using Cx = C<T>;
+  using F = FftC<T, LOGL>;
+  constexpr int L = F::L, L8 = F::L8, M = L;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[3 * 32];
+  __shared__ int lastflag;
+  Cx* sm = reinterpret_cast<Cx*>(smem_raw);
+  Scalars* sc = a.sc;
+  if (MODE != C_PLAIN && MODE != C_GAP) {
+    if (sc->done) return;
+  }
+  const int nb = a.pl.nbA, lognb = a.pl.lognbA, rs = a.pl.gA.rs;
+  const int nx = a.pl.nx, ny = a.pl.ny;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int b = tid >> (LOGL - 3), t = tid & (L8 - 1);
+  const int G = (ny + nb - 1) / nb;
+  const Cx* W = reinterpret_cast<const Cx*>(a.W);
+  const Cx* tws = reinterpret_cast<const Cx*>(a.twS);
+  const Cx* tw = reinterpret_cast<const Cx*>(a.twA);
+  const int* sp = a.spA;
+  Cx* buf = sm + b * rs;
+  // shared memory: transform rows | W staging [(M+1) x nb] | epilogue staging
+  const size_t off_w = (sizeof(Cx) * (size_t)nb * rs + 15) & ~(size_t)15;
+  Cx* wst = reinterpret_cast<Cx*>(smem_raw + off_w);
+  const size_t off_e = off_w + ((sizeof(Cx) * (size_t)(M + 1) * nb + 15) & ~(size_t)15);
+  T* st = reinterpret_cast<T*>(smem_raw + off_e);
+  uint8_t* ss = reinterpret_cast<uint8_t*>(st) + (size_t)EpiStage<MODE>::nT * sizeof(T) * nb * nx;
+
+  auto prefetch_w = [&](int gg) {
+    const int r0 = gg * nb, rows = min(nb, ny - r0);
+    for (int q = tid; q < (M + 1) << lognb; q += nthr) {
+      const int k = q >> lognb, bb = q & (nb - 1);
+      if (bb < rows) cp_async_cx<Cx>(wst + q, W + (size_t)k * a.rows_w + r0 + bb);
+    }
+    cp_async_commit();
+  };
+  auto prefetch_e = [&](int gg) {
+    const int r0 = gg * nb, rows = min(nb, ny - r0);
+    const int cpr = nx * (int)sizeof(T) / 16;
+#pragma unroll
+    for (int f = 0; f < EpiStage<MODE>::nT; ++f) {
+      const T* src = (MODE == C_PK_G) ? (f == 0 ? a.f.c : a.f.p) : (MODE == C_CG_R ? a.f.t : a.f.c);
+      for (int q = tid; q < cpr * rows; q += nthr) {
+        const int bb = q / cpr, ch = q - bb * cpr;
+        cp_async16(reinterpret_cast<char*>(st + ((size_t)f * nb + bb) * nx) + 16 * ch,
+                   reinterpret_cast<const char*>(src + (size_t)(r0 + bb) * nx) + 16 * ch);
+      }
+    }
+    if (EpiStage<MODE>::S) {
+      const int cps = nx / 16;
+      for (int q = tid; q < cps * rows; q += nthr) {
+        const int bb = q / cps, ch = q - bb * cps;
+        cp_async16(ss + (size_t)bb * nx + 16 * ch, a.f.S + (size_t)(r0 + bb) * nx + 16 * ch);
+      }
+    }
+    cp_async_commit();
+  };
+
+  const T us = (T)a.uscale;
+  T acc[3] = {0, 0, 0};
+  const int half = (nx + 1) >> 1;
+  int g = blockIdx.x;
+  if (g < G) { prefetch_w(g); prefetch_e(g); }
+  for (; g < G; g += gridDim.x) {
+    const int row0 = g * nb;
+    cp_async_wait_1();  // W of this group (its epilogue fields may still be in flight)
+    __syncthreads();
+    // rebuild the packed half-length spectrum from the staged W rows
+#pragma unroll 2
+    for (int idx = tid; idx < ((M >> 1) + 1) << lognb; idx += nthr) {
+      const int k = idx >> lognb, bb = idx & (nb - 1);
+      const Cx xk = wst[(k << lognb) + bb], xm = wst[((M - k) << lognb) + bb];
+      Cx* s = sm + bb * rs;
+      const Cx wk = conj<T>(__ldg(tws + k));
+      {
+        const Cx E = add<T>(xk, conj<T>(xm));
+        const Cx O = mul<T>(sub<T>(xk, conj<T>(xm)), wk);
+        s[__ldg(sp + k)] = add<T>(E, mul_si<T, 1>(O));
+      }
+      if (k != 0 && k != M - k) {
+        const Cx wm = mk<T>(-wk.x, wk.y);
+        const Cx E = add<T>(xm, conj<T>(xk));
+        const Cx O = mul<T>(sub<T>(xm, conj<T>(xk)), wm);
+        s[__ldg(sp + M - k)] = add<T>(E, mul_si<T, 1>(O));
+      }
+    }
+    __syncthreads();  // W staging consumed
+    const int gn = g + gridDim.x;
+    if (gn < G) prefetch_w(gn);
+#pragma unroll
+    for (int ls = 0; ls <= F::LS_TOP; ls += 3) {
+      F::dit(buf, t, ls, tw);
+      __syncthreads();
+    }
+    if (gn < G) cp_async_wait_1(); else cp_async_wait_all();  // epilogue fields of this group
+    __syncthreads();
+    const int row = row0 + b;
+    const bool act = row < ny;
+    const size_t rowoff = (size_t)row * nx;
+    EIn<T> ein[8][2];
+    if (MODE != C_PLAIN) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        if (!F::first_half(e)) continue;
+        const int n = F::n0(t, e);
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+          if (act && n < half && 2 * n + h < nx) {
+            if (EpiStage<MODE>::any) epi_gather_staged<T, MODE>(st, ss, b, 2 * n + h, nx, nb, ein[e][h]);
+            else epi_gather<T, MODE>(a, rowoff + 2 * n + h, ein[e][h]);
+          }
+      }
+    }
+    Cx v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = buf[F::ix0(t, e)];
+    F::stage0_inv(v, t, tw);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      if (!F::first_half(e)) continue;
+      const int n = F::n0(t, e);
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        if (act && n < half && 2 * n + h < nx)
+          epi_apply<T, MODE>(a, rowoff + 2 * n + h, us * (h ? v[e].y : v[e].x), ein[e][h], acc);
+    }
+    __syncthreads();  // epilogue staging and transform rows consumed
+    if (gn < G && EpiStage<MODE>::any) prefetch_e(gn);
+    else if (gn < G) cp_async_commit();  // keep the two-groups-per-iteration accounting
+  }
+  cp_async_wait_all();
+  if (MODE == C_PLAIN || MODE == C_GAP) return;
+  double vv[2] = {(double)acc[0], (double)acc[1]};
+  block_sum<2>(vv, red);
+  if (tid == 0) {
+    double* pp = a.partC + 4 * blockIdx.x;
+    pp[0] = vv[0]; pp[1] = vv[1];
+  }
+  if (!last_block_arrival(MODE == C_PK_G ? &sc->cnt_c : &sc->cnt_a, &lastflag)) return;
+  double s2[2];
+  sum_partials<2>(a.partC, gridDim.x, s2, red);
+  double s3[3] = {0, 0, 0};
+  if (MODE == C_PK_G) sum_partials<3>(a.partA, __ldcg(&sc->nA), s3, red);
+  if (tid != 0) return;
+  pass_c_finalize<MODE>(sc, s2, s3);
+}
+
 // ---------------------------------------------------------------------------
 // Elementwise kernels (grid-stride, FP64 partials per CTA, last block reduces).
 
@@ -663,18 +1066,47 @@ __global__ void k_pk_init(int n, const double* __restrict__ h64, double d, T* __
 }
 
 template <typename T>
+__device__ __forceinline__ T cg_update_one(T* __restrict__ p, T* __restrict__ g, const T* __restrict__ t,
+                                           const T* __restrict__ r, int i, T tau) {
+  const T gv = g[i] - tau * r[i];
+  p[i] -= tau * t[i];
+  g[i] = gv;
+  return gv * gv;
+}
+
+// p -= tau t, g -= tau r on the set (t and r vanish off it); last block forms
+// the new G, beta and the convergence test.  Four elements per thread and
+// trip through vector loads when the pointers allow it.
+template <typename T>
 __global__ void k_cg_update(int n, Fields<T> f, double* part, Scalars* sc) {
   __shared__ double red[3 * 32];
   __shared__ int lastflag;
   if (sc->done) return;
   const T tau = (T)sc->tau;
   T acc = 0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const T tv = f.t[i], rv = f.r[i];
-    f.p[i] -= tau * tv;
-    const T gv = f.g[i] - tau * rv;
-    f.g[i] = gv;
-    acc += gv * gv;
+  T* __restrict__ p = f.p;
+  T* __restrict__ g = f.g;
+  const T* __restrict__ t = f.t;
+  const T* __restrict__ r = f.r;
+  if (sizeof(T) == 4 && (n & 3) == 0) {
+    using V = float4;
+    V* pv = reinterpret_cast<V*>(p);
+    V* gv = reinterpret_cast<V*>(g);
+    const V* tv = reinterpret_cast<const V*>(t);
+    const V* rv = reinterpret_cast<const V*>(r);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (n >> 2); i += gridDim.x * blockDim.x) {
+      V a = pv[i], b = gv[i];
+      const V c = tv[i], d = rv[i];
+      const float tf = (float)tau;
+      a.x -= tf * c.x; a.y -= tf * c.y; a.z -= tf * c.z; a.w -= tf * c.w;
+      b.x -= tf * d.x; b.y -= tf * d.y; b.z -= tf * d.z; b.w -= tf * d.w;
+      pv[i] = a;
+      gv[i] = b;
+      acc += (T)(b.x * b.x + b.y * b.y + b.z * b.z + b.w * b.w);
+    }
+  } else {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+      acc += cg_update_one<T>(p, g, t, r, i, tau);
   }
   double v[1] = {(double)acc};
   block_sum<1>(v, red);
@@ -750,13 +1182,24 @@ __global__ void k_stats(int n, const T* p, const T* g, const uint8_t* S, int use
     pp[0] = v[0]; pp[1] = v[1]; pp[2] = a1; pp[3] = a2;
   }
   if (!last_block_arrival(counter, &lastflag)) return;
+  // fixed-order parallel reduction of the per-CTA partials
+  double s0 = 0, s1 = 0, x1 = 0, x2 = 0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    s0 += __ldcg(part + 4 * b); s1 += __ldcg(part + 4 * b + 1);
+    x1 = fmax(x1, __ldcg(part + 4 * b + 2)); x2 = fmax(x2, __ldcg(part + 4 * b + 3));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    x1 = fmax(x1, __shfl_down_sync(0xffffffffu, x1, o));
+    x2 = fmax(x2, __shfl_down_sync(0xffffffffu, x2, o));
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) { redm[0][threadIdx.x >> 5] = x1; redm[1][threadIdx.x >> 5] = x2; }
+  double v2[2] = {s0, s1};
+  block_sum<2>(v2, red);
   if (threadIdx.x == 0) {
-    double s0 = 0, s1 = 0, x1 = 0, x2 = 0;
-    for (int b = 0; b < (int)gridDim.x; ++b) {
-      s0 += __ldcg(part + 4 * b); s1 += __ldcg(part + 4 * b + 1);
-      x1 = fmax(x1, __ldcg(part + 4 * b + 2)); x2 = fmax(x2, __ldcg(part + 4 * b + 3));
-    }
-    out[0] = s0; out[1] = s1; out[2] = x1; out[3] = x2;
+    double a1 = 0, a2 = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a1 = fmax(a1, redm[0][w]); a2 = fmax(a2, redm[1][w]); }
+    out[0] = v2[0]; out[1] = v2[1]; out[2] = a1; out[3] = a2;
     *counter = 0;
   }
 }
@@ -793,9 +1236,48 @@ __global__ void k_mask_field(T* x, const uint8_t* S, size_t n) {
 #define BEM_LOGL_CASES_A(X) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12)
 #define BEM_LOGL_CASES_B(X) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13)
 
+// Resident CTAs per SM of a kernel at a launch shape (cached per shape).
+template <typename K>
+int resident_ctas(K kernel, int threads, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::tuple<const void*, int, size_t>, int> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  const auto key = std::make_tuple((const void*)kernel, threads, smem);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    n = 1;
+  }
+  if (n < 1) n = 1;
+  cache[key] = n;
+  return n;
+}
+
+#ifndef BEM_PERSISTENT
+#define BEM_PERSISTENT 1
+#endif
+
 template <typename T, int MODE>
 void launch_a_mode(const PassArgs<T>& a, cudaStream_t s) {
-  const dim3 grid((a.nrows_in + a.pl.nbA - 1) / a.pl.nbA), block(a.pl.threadsA);
+  const dim3 block(a.pl.threadsA);
+  const int groups = (a.nrows_in + a.pl.nbA - 1) / a.pl.nbA;
+  if (BEM_PERSISTENT && MODE != A_TORUS && (a.ncols_in & 15) == 0) {
+    const size_t smem = ((a.pl.smemA + 15) & ~(size_t)15) + pro_stage_bytes<T, MODE>(a.pl.nbA, a.ncols_in);
+    switch (a.pl.gA.logL) {
+#define BEM_CASE(LG)                                                                        \
+  case LG: {                                                                                \
+    const int occ = resident_ctas(k_pass_ap<T, MODE, LG>, a.pl.threadsA, smem);            \
+    const int grid = std::min(groups, a.pl.nsm * occ);                                      \
+    k_pass_ap<T, MODE, LG><<<grid, block, smem, s>>>(a);                                    \
+  } break;
+      BEM_LOGL_CASES_A(BEM_CASE)
+#undef BEM_CASE
+    }
+    return;
+  }
+  const dim3 grid(groups);
   switch (a.pl.gA.logL) {
 #define BEM_CASE(LG) case LG: k_pass_a<T, MODE, LG><<<grid, block, a.pl.smemA, s>>>(a); break;
     BEM_LOGL_CASES_A(BEM_CASE)
@@ -813,9 +1295,28 @@ void launch_b_mode(const PassArgs<T>& a, cudaStream_t s) {
 }
 template <typename T, int MODE>
 void launch_c_mode(const PassArgs<T>& a, cudaStream_t s) {
-  const dim3 grid(a.pl.gridA), block(a.pl.threadsA);
+  const dim3 block(a.pl.threadsA);
+  const int groups = a.pl.gridA;
+  if (BEM_PERSISTENT && (a.pl.nx & 15) == 0) {
+    const size_t smem = ((a.pl.smemC + 15) & ~(size_t)15) +
+                        ((sizeof(C<T>) * (size_t)(a.pl.M + 1) * a.pl.nbA + 15) & ~(size_t)15) +
+                        epi_stage_bytes<T, MODE>(a.pl.nbA, a.pl.nx);
+    switch (a.pl.gA.logL) {
+#define BEM_CASE(LG)                                                                        \
+  case LG: {                                                                                \
+    const int occ = resident_ctas(k_pass_cp<T, MODE, LG>, a.pl.threadsA, smem);            \
+    const int grid = std::min(groups, a.pl.nsm * occ);                                      \
+    k_pass_cp<T, MODE, LG><<<grid, block, smem, s>>>(a);                                    \
+  } break;
+      BEM_LOGL_CASES_A(BEM_CASE)
+#undef BEM_CASE
+    }
+    return;
+  }
+  const dim3 grid(groups);
+  const size_t smem = ((a.pl.smemC + 15) & ~(size_t)15) + epi_stage_bytes<T, MODE>(a.pl.nbA, a.pl.nx);
   switch (a.pl.gA.logL) {
-#define BEM_CASE(LG) case LG: k_pass_c<T, MODE, LG><<<grid, block, a.pl.smemC, s>>>(a); break;
+#define BEM_CASE(LG) case LG: k_pass_c<T, MODE, LG><<<grid, block, smem, s>>>(a); break;
     BEM_LOGL_CASES_A(BEM_CASE)
 #undef BEM_CASE
   }
@@ -850,11 +1351,19 @@ void launch_pass_c(const PassArgs<T>& a, int mode, cudaStream_t s) {
   }
 }
 
-// Opt every pass kernel into `bytes` of dynamic shared memory (the static
-// reduction scratch counts against the same 227 KB per block, so the request
-// is sized to what the plans need).  Returns the first failure.
+// Opt every pass kernel into the largest dynamic shared memory the SM allows
+// next to its static reduction scratch (227 KB per block in total).  `bytes`
+// caps the request.  Returns the first failure.
+template <typename K>
+cudaError_t set_smem_max(K kernel, int bytes) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  const int lim = 227 * 1024 - (int)fa.sharedSizeBytes;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes < lim ? bytes : lim);
+}
 #define BEM_ATTR(fn) \
-  if ((r = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess && e == cudaSuccess) e = r;
+  if ((r = set_smem_max(fn, bytes)) != cudaSuccess && e == cudaSuccess) e = r;
 template <typename T>
 cudaError_t set_smem_attrs_a(int bytes) {
   cudaError_t e = cudaSuccess, r;
@@ -863,6 +1372,10 @@ cudaError_t set_smem_attrs_a(int bytes) {
   BEM_ATTR((k_pass_a<T, A_PK_P, LG>))         \
   BEM_ATTR((k_pass_a<T, A_PK_T, LG>))         \
   BEM_ATTR((k_pass_a<T, A_CG_T, LG>))         \
+  BEM_ATTR((k_pass_ap<T, A_PLAIN, LG>))       \
+  BEM_ATTR((k_pass_ap<T, A_PK_P, LG>))        \
+  BEM_ATTR((k_pass_ap<T, A_PK_T, LG>))        \
+  BEM_ATTR((k_pass_ap<T, A_CG_T, LG>))        \
   if constexpr (sizeof(T) == 8) { BEM_ATTR((k_pass_a<T, A_TORUS, LG>)) }
   BEM_LOGL_CASES_A(BEM_CASE)
 #undef BEM_CASE
@@ -885,7 +1398,13 @@ cudaError_t set_smem_attrs_c(int bytes) {
   BEM_ATTR((k_pass_c<T, C_PK_R, LG>))         \
   BEM_ATTR((k_pass_c<T, C_CG_R, LG>))         \
   BEM_ATTR((k_pass_c<T, C_CG_G, LG>))         \
-  BEM_ATTR((k_pass_c<T, C_GAP, LG>))
+  BEM_ATTR((k_pass_c<T, C_GAP, LG>))          \
+  BEM_ATTR((k_pass_cp<T, C_PLAIN, LG>))       \
+  BEM_ATTR((k_pass_cp<T, C_PK_G, LG>))        \
+  BEM_ATTR((k_pass_cp<T, C_PK_R, LG>))        \
+  BEM_ATTR((k_pass_cp<T, C_CG_R, LG>))        \
+  BEM_ATTR((k_pass_cp<T, C_CG_G, LG>))        \
+  BEM_ATTR((k_pass_cp<T, C_GAP, LG>))
   BEM_LOGL_CASES_A(BEM_CASE)
 #undef BEM_CASE
   return e;

@@ -530,8 +530,8 @@ extern "C" int bem_create(int Nx, int Ny, double dx, double dy, double k, double
     return cleanup(fail(BEM_ECUDA, "stream creation failed"));
   static bool attrs_done = false;
   if (!attrs_done) {
-    // plans never ask for more than 128 KB + one row of dynamic shared memory
-    const int smem_max = 136 * 1024;
+    // every kernel may use as much dynamic shared memory as the SM allows
+    const int smem_max = 227 * 1024;
     cudaError_t ea = set_smem_attrs_a<float>(smem_max);
     if (ea == cudaSuccess) ea = set_smem_attrs_b<float>(smem_max);
     if (ea == cudaSuccess) ea = set_smem_attrs_c<float>(smem_max);
@@ -550,6 +550,12 @@ extern "C" int bem_create(int Nx, int Ny, double dx, double dy, double k, double
   h->py = pow2_at_least(2 * Ny < 32 ? 32 : 2 * Ny);
   h->plan32 = make_plan(Nx, Ny, h->px, h->py, 4);
   h->plan64 = make_plan(Nx, Ny, h->px, h->py, 8);
+  {
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || nsm < 1)
+      return cleanup(fail(BEM_ECUDA, "cannot query the SM count"));
+    h->plan32.nsm = h->plan64.nsm = nsm;
+  }
   const int M = h->px / 2, hyq = h->py / 2 + 1;
   const size_t n = (size_t)Nx * Ny;
   int rc;
