@@ -113,6 +113,25 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def pass_flops(nx, ny, px, py):
+    """Algorithmic FP32 flops of one launch of each transform pass (5 L log2 L per
+    complex FFT of length L, halved for a transform with half its inputs zero
+    or half its outputs dropped), plus the split/spectrum work."""
+    M = px // 2
+    lm, lp = math.log2(M), math.log2(py)
+    fft_m = 5 * M * lm
+    fft_p = 5 * py * lp
+    a = ny * (0.5 * fft_m + 20 * M)            # row FFT, half the inputs zero, split
+    b = (M + 1) * (2 * 0.5 * fft_p + 8 * py)    # column FFT and its inverse, pruned, multiply
+    c = ny * (0.5 * fft_m + 20 * M)            # packing, row inverse keeping half
+    return {"A": a, "B": b, "C": c}
+
+
+def fp32_peak_tflops(sm_mhz):
+    """FP32 vector peak: 152 SMs x 128 lanes x 2 flops (FMA) x clock."""
+    return 152 * 128 * 2 * (sm_mhz or 2070.0) * 1e6 / 1e12
+
+
 def pass_bytes(nx, ny, px, py, mode):
     """Algorithmic HBM bytes of one launch of each transform pass, FP32 fields.
 
@@ -281,6 +300,7 @@ def main():
     bpk = pass_bytes(N, N, info.Px, info.Py, "pk")
     bcg = pass_bytes(N, N, info.Px, info.Py, "cg")
     bytes_dom = (1 - frac_cg) * bpk[names[dom]] + frac_cg * bcg[names[dom]]
+    flops_dom = pass_flops(N, N, info.Px, info.Py)[names[dom]]
     achieved = bytes_dom / (avg_ms[dom] * 1e-3) / 1e9
 
     forces = [r.force for r in results]
@@ -305,7 +325,12 @@ def main():
                      "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
                      "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
                      "avg_ms": {k: v for k, v in zip(names, avg_ms)}, "timed_launches": pass_n,
-                     "bytes_per_launch": bytes_dom},
+                     "bytes_per_launch": bytes_dom,
+                     "alu": {"achieved": flops_dom / (avg_ms[dom] * 1e-3) / 1e12,
+                             "peak": fp32_peak_tflops(clocks.get("sm_max_mhz")), "unit": "TFLOP/s",
+                             "frac": flops_dom / (avg_ms[dom] * 1e-3) / 1e12
+                             / fp32_peak_tflops(clocks.get("sm_max_mhz")),
+                             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}},
         "clocks": clocks,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 8 * N * N + 8 * len(ds),
                 "d2h_bytes_per_step": 8 * N * N + 56 * len(ds)},
