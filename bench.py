@@ -153,6 +153,23 @@ def pass_bytes(nx, ny, px, py, mode):
     return {"A": a, "B": b, "C": c}
 
 
+def aggregate(elapsed_s, iters, world, device):
+    """Whole-job figures over ranks: (max elapsed seconds, total iterations).
+
+    Every rank calls it after its timed region; with one rank it is the identity.
+    """
+    if world <= 1:
+        return float(elapsed_s), float(iters)
+    import torch
+    import torch.distributed as dist
+    el = torch.tensor([float(elapsed_s)], dtype=torch.float64, device=device)
+    it = torch.tensor([float(iters)], dtype=torch.float64, device=device)
+    dist.barrier()
+    dist.all_reduce(el, op=dist.ReduceOp.MAX)
+    dist.all_reduce(it, op=dist.ReduceOp.SUM)
+    return float(el.item()), float(it.item())
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -269,14 +286,8 @@ def main():
     launches = h.info().kernel_launches - launches0
     pass_ms, pass_n, pass_cg = h.pass_times(reset=True)
     elapsed = sum(step_ms) / 1e3
-    el_t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
-    it_t = torch.tensor([float(iters_total)], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.barrier()
-        dist.all_reduce(el_t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(it_t, op=dist.ReduceOp.SUM)
-    elapsed_max = float(el_t.item())
-    value = float(it_t.item()) / elapsed_max
+    elapsed_max, iters_all = aggregate(elapsed, iters_total, world, "cuda")
+    value = iters_all / elapsed_max
 
     # e2e through the C ABI with pinned host buffers
     prof_pin = torch.from_numpy(prof_h).pin_memory()
