@@ -23,6 +23,8 @@
 #ifndef BEM_GB300_H
 #define BEM_GB300_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -119,6 +121,62 @@ int bem_sweep(bem_handle h, const double *profile, const double *d_steps, int ns
               double dgamma, const bem_opts *opts, bem_result *per_step, double *final_pressure);
 
 /* ---------------------------------------------------------------------------
+ * Request server: many independent solves in flight on the current device.
+ *
+ * bem_server_create starts nworkers host threads; each runs one job at a time
+ * on its own CUDA stream, so up to nworkers solves overlap on the GPU.  A job
+ * is admitted when its device-memory footprint fits hbm_budget_bytes next to
+ * the running jobs and the cached handles; a job that does not fit yet lets
+ * later jobs that do fit go first, and idle cached handles are evicted least
+ * recently used first.  Handles (influence spectra) are cached by
+ * (Nx, Ny, dx, dy, k) and reused with bem_set_material for nu, E0, c0.
+ * Results are deterministic: a job's outputs do not depend on what else runs.
+ *
+ * bem_job: the arguments of one bem_sweep (a single solve is nsteps = 1; an
+ * adhesive solve is {d_preload, d}).  The job struct is copied on submit; the
+ * arrays it points to (profile, d_steps, per_step, final_pressure) belong to
+ * the caller and must stay valid until the job's completion is polled.
+ * opts.stream is ignored (each worker uses its handle's stream).
+ * bem_server_submit: BEM_EINVAL on bad arguments, BEM_ENOMEM if the job alone
+ *   exceeds the budget.
+ * bem_server_poll: moves up to max completion records into out, waiting up to
+ *   wait_ms for the first; returns how many.  Times are seconds since create.
+ * bem_server_pending: jobs queued or running.
+ * bem_server_bytes: device bytes accounted to cached and running handles.
+ * bem_server_footprint: the bytes admission reserves for a job on an Nx x Ny
+ *   grid (a handle after FP32 and FP64 solves plus its set-up workspace);
+ *   0 for a grid outside 2..4096.
+ * bem_server_destroy: finishes the queued jobs, then frees everything. */
+typedef struct {
+  int Nx, Ny;
+  double dx, dy, k, nu, E0, c0;
+  const double *profile;
+  const double *d_steps;
+  int nsteps;
+  double dgamma;
+  bem_opts opts;
+  bem_result *per_step;
+  double *final_pressure;
+  long long tag;
+} bem_job;
+
+typedef struct {
+  long long tag;
+  int status;
+  double t_submit, t_start, t_end;
+} bem_completion;
+
+typedef struct bem_server *bem_server_handle;
+
+int bem_server_create(int nworkers, size_t hbm_budget_bytes, bem_server_handle *out);
+int bem_server_submit(bem_server_handle s, const bem_job *job);
+int bem_server_poll(bem_server_handle s, bem_completion *out, int max, int wait_ms);
+int bem_server_pending(bem_server_handle s);
+size_t bem_server_bytes(bem_server_handle s);
+size_t bem_server_footprint(int Nx, int Ny);
+void bem_server_destroy(bem_server_handle s);
+
+/* ---------------------------------------------------------------------------
  * Building blocks, exposed for verification.
  *
  * bem_influence_table: copy the FP64 influence coefficients K(di, dj) of Eq. 9
@@ -142,6 +200,11 @@ typedef struct {
 } bem_info;
 
 int bem_get_info(bem_handle h, bem_info *info);
+
+/* Change nu, E0, c0 of a handle (k, the grid and the influence spectrum stay):
+ * only the prefactor A of Eq. 12 depends on them.  Same validation as
+ * bem_create; BEM_EINVAL leaves the handle unchanged. */
+int bem_set_material(bem_handle h, double nu, double E0, double c0);
 
 /* Accumulated device time of the transform passes recorded under
  * BEM_FLAG_TIME_PASSES: ms[0..2] = total milliseconds of passes A (row FFT and

@@ -63,6 +63,20 @@ class Info(ctypes.Structure):
                 ("device_bytes", ctypes.c_size_t), ("kernel_launches", ctypes.c_ulonglong)]
 
 
+class Job(ctypes.Structure):
+    _fields_ = [("Nx", ctypes.c_int), ("Ny", ctypes.c_int), ("dx", ctypes.c_double),
+                ("dy", ctypes.c_double), ("k", ctypes.c_double), ("nu", ctypes.c_double),
+                ("E0", ctypes.c_double), ("c0", ctypes.c_double), ("profile", ctypes.c_void_p),
+                ("d_steps", ctypes.c_void_p), ("nsteps", ctypes.c_int), ("dgamma", ctypes.c_double),
+                ("opts", Opts), ("per_step", ctypes.c_void_p), ("final_pressure", ctypes.c_void_p),
+                ("tag", ctypes.c_longlong)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_longlong), ("status", ctypes.c_int), ("t_submit", ctypes.c_double),
+                ("t_start", ctypes.c_double), ("t_end", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -95,6 +109,17 @@ def load_library(path: str = LIB_PATH):
     lib.bem_c1_corrected.argtypes = [ctypes.c_double]
     lib.bem_p_crit.restype = ctypes.c_double
     lib.bem_p_crit.argtypes = [ctypes.c_double] * 6
+    lib.bem_set_material.argtypes = [vp] + [ctypes.c_double] * 3
+    lib.bem_server_create.argtypes = [ip, ctypes.c_size_t, ctypes.POINTER(vp)]
+    lib.bem_server_submit.argtypes = [vp, ctypes.POINTER(Job)]
+    lib.bem_server_poll.argtypes = [vp, ctypes.POINTER(Completion), ip, ip]
+    lib.bem_server_pending.argtypes = [vp]
+    lib.bem_server_bytes.argtypes = [vp]
+    lib.bem_server_bytes.restype = ctypes.c_size_t
+    lib.bem_server_footprint.argtypes = [ip, ip]
+    lib.bem_server_footprint.restype = ctypes.c_size_t
+    lib.bem_server_destroy.argtypes = [vp]
+    lib.bem_server_destroy.restype = None
     _lib = lib
     return lib
 
@@ -216,6 +241,9 @@ class Handle:
                                            _ptr(out, self.n, writable=True)))
         return out
 
+    def set_material(self, nu, E0=1.0, c0=1.0):
+        _check(load_library().bem_set_material(self._h, nu, E0, c0))
+
     def solve(self, profile, d, dgamma=0.0, d_preload=None, pressure_out=None, check=True, **opts):
         res = Result()
         o = make_opts(**opts)
@@ -237,3 +265,83 @@ class Handle:
         if check:
             _check(rc, allow=(BEM_ENOCONV,))
         return list(res), rc
+
+
+class Server:
+    """bem_server_*: independent sweeps run by native worker threads.
+
+    ``submit`` copies the job description and keeps the arrays it points to
+    alive until ``poll`` returns the job's completion, which carries the
+    per-step results and the final pressure (if one was asked for).
+    """
+
+    def __init__(self, nworkers=4, hbm_budget_bytes=16 << 30):
+        lib = load_library()
+        s = ctypes.c_void_p()
+        _check(lib.bem_server_create(nworkers, hbm_budget_bytes, ctypes.byref(s)))
+        self._s = s
+        self._live = {}
+        self._next = 0
+
+    def submit(self, nx, ny, dx, dy, k, nu, profile, d_steps, dgamma=0.0, E0=1.0, c0=1.0,
+               final_pressure=None, **opts):
+        ds = np.ascontiguousarray(np.asarray(d_steps, dtype=np.float64))
+        res = (Result * len(ds))()
+        tag = self._next
+        self._next += 1
+        fp = _ptr(final_pressure, nx * ny, writable=True) if final_pressure is not None else None
+        job = Job(nx, ny, dx, dy, k, nu, E0, c0, _ptr(profile, nx * ny), _ptr(ds), len(ds), dgamma,
+                  make_opts(**opts), ctypes.cast(res, ctypes.c_void_p), fp, tag)
+        self._live[tag] = (profile, ds, res, final_pressure)
+        _check(load_library().bem_server_submit(self._s, ctypes.byref(job)))
+        return tag
+
+    def poll(self, max_n=64, wait_ms=0):
+        """Completed jobs as dicts: tag, status, t_submit/t_start/t_end (s), results, pressure."""
+        buf = (Completion * max_n)()
+        n = load_library().bem_server_poll(self._s, buf, max_n, wait_ms)
+        if n < 0:
+            _check(n)
+        out = []
+        for c in buf[:n]:
+            profile, ds, res, fp = self._live.pop(c.tag)
+            out.append({"tag": c.tag, "status": c.status, "t_submit": c.t_submit, "t_start": c.t_start,
+                        "t_end": c.t_end, "results": list(res), "final_pressure": fp})
+        return out
+
+    def pending(self):
+        return load_library().bem_server_pending(self._s)
+
+    def device_bytes(self):
+        return load_library().bem_server_bytes(self._s)
+
+    @staticmethod
+    def footprint(nx, ny):
+        return load_library().bem_server_footprint(nx, ny)
+
+    def drain(self, timeout_s=600.0):
+        """Poll until every submitted job has completed; returns their completions."""
+        import time
+        out, t_end = [], time.monotonic() + timeout_s
+        while self._live:
+            if time.monotonic() > t_end:
+                raise TimeoutError(f"{len(self._live)} jobs still pending")
+            out += self.poll(wait_ms=100)
+        return out
+
+    def close(self):
+        if getattr(self, "_s", None):
+            load_library().bem_server_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -7,6 +7,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
 #include <string>
 
 #include "bem.h"
@@ -528,20 +529,26 @@ extern "C" int bem_create(int Nx, int Ny, double dx, double dy, double k, double
   if (cudaGetDevice(&h->device) != cudaSuccess) return cleanup(fail(BEM_ECUDA, "no CUDA device"));
   if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess)
     return cleanup(fail(BEM_ECUDA, "stream creation failed"));
-  static bool attrs_done = false;
-  if (!attrs_done) {
-    // every kernel may use as much dynamic shared memory as the SM allows
-    const int smem_max = 227 * 1024;
-    cudaError_t ea = set_smem_attrs_a<float>(smem_max);
-    if (ea == cudaSuccess) ea = set_smem_attrs_b<float>(smem_max);
-    if (ea == cudaSuccess) ea = set_smem_attrs_c<float>(smem_max);
-    if (ea == cudaSuccess) ea = set_smem_attrs_a<double>(smem_max);
-    if (ea == cudaSuccess) ea = set_smem_attrs_b<double>(smem_max);
-    if (ea == cudaSuccess) ea = set_smem_attrs_c<double>(smem_max);
-    if (ea != cudaSuccess)
-      return cleanup(fail(BEM_ECUDA, "shared-memory opt-in failed: %s", cudaGetErrorString(ea)));
-    if (influence_init_nodes() != 0) return cleanup(fail(BEM_ECUDA, "quadrature nodes upload failed"));
-    attrs_done = true;
+  {
+    // once per device and process: shared-memory opt-ins and quadrature nodes
+    static std::mutex init_mu;
+    static bool init_done[64] = {};
+    std::lock_guard<std::mutex> lk(init_mu);
+    if (h->device < 0 || h->device >= 64) return cleanup(fail(BEM_ECUDA, "device index %d unsupported", h->device));
+    if (!init_done[h->device]) {
+      // every kernel may use as much dynamic shared memory as the SM allows
+      const int smem_max = 227 * 1024;
+      cudaError_t ea = set_smem_attrs_a<float>(smem_max);
+      if (ea == cudaSuccess) ea = set_smem_attrs_b<float>(smem_max);
+      if (ea == cudaSuccess) ea = set_smem_attrs_c<float>(smem_max);
+      if (ea == cudaSuccess) ea = set_smem_attrs_a<double>(smem_max);
+      if (ea == cudaSuccess) ea = set_smem_attrs_b<double>(smem_max);
+      if (ea == cudaSuccess) ea = set_smem_attrs_c<double>(smem_max);
+      if (ea != cudaSuccess)
+        return cleanup(fail(BEM_ECUDA, "shared-memory opt-in failed: %s", cudaGetErrorString(ea)));
+      if (influence_init_nodes() != 0) return cleanup(fail(BEM_ECUDA, "quadrature nodes upload failed"));
+      init_done[h->device] = true;
+    }
   }
   h->nx = Nx; h->ny = Ny; h->dx = dx; h->dy = dy; h->k = k; h->nu = nu; h->E0 = E0; h->c0 = c0;
   h->alpha = alpha;
@@ -657,6 +664,24 @@ extern "C" int bem_get_info(bem_handle h, bem_info* info) {
   info->dx = h->dx; info->dy = h->dy; info->k = h->k; info->nu = h->nu; info->E0 = h->E0; info->c0 = h->c0;
   info->alpha = h->alpha; info->compliance = h->A; info->device_bytes = h->bytes;
   info->kernel_launches = h->launches;
+  return BEM_OK;
+}
+
+extern "C" int bem_set_material(bem_handle h, double nu, double E0, double c0) {
+  if (!h) return fail(BEM_EINVAL, "NULL handle");
+  if (!(nu > -1.0 && nu <= 0.5)) return fail(BEM_EINVAL, "nu=%g outside (-1, 0.5]", nu);
+  if (!(E0 > 0) || !(c0 > 0)) return fail(BEM_EINVAL, "E0 and c0 must be > 0");
+  const double alpha = bem_alpha(h->k, nu);
+  if (!(alpha > 0) || !isfinite(alpha)) return fail(BEM_EINVAL, "alpha(k=%g, nu=%g) undefined", h->k, nu);
+  const double A = alpha * (1.0 - nu * nu) * pow(c0, h->k) / E0;
+  if (A == h->A && nu == h->nu && E0 == h->E0 && c0 == h->c0) return BEM_OK;
+  h->nu = nu; h->E0 = E0; h->c0 = c0; h->alpha = alpha; h->A = A;
+  // the captured CG graphs carry A/(Px Py) as a kernel argument: recapture lazily
+  CK(cudaStreamSynchronize(h->stream));
+  for (int t = 0; t < 2; ++t) {
+    for (cudaGraphExec_t* g : {&h->f32.pk_graph[t], &h->f32.cg_graph[t], &h->f64.pk_graph[t], &h->f64.cg_graph[t]})
+      if (*g) { cudaGraphExecDestroy(*g); *g = nullptr; }
+  }
   return BEM_OK;
 }
 

@@ -15,6 +15,10 @@ Profiles:
                               PSD ~ q^(-2(1+H)) between q0 and q1, random phases,
                               rms slope fixed; h = max z - z.
 
+Request mixes (parameters only; profiles are built per job by job_profile):
+  batch_jobs(count, seed)          independent solves of mixed size, k and adhesion
+  serving_requests(count, seed)    the same kind of solves with Poisson arrival times
+
 EXCLUDED (1e3, far above any indentation used) marks cells where the
 indenter has no surface, so they can never come into contact.
 """
@@ -108,3 +112,58 @@ def random_pressure(nx: int, ny: int | None = None, seed: int = 0, density: floa
     if density < 1.0:
         p = np.where(rng.random((ny, nx)) < density, p, 0.0)
     return p
+
+
+def _job(rng, n: int, index: int, seed_base: int) -> dict:
+    """One solve: grid n x n on the unit square, k ~ U[-0.8, 0.8], nu = 0.3;
+    paraboloid R = 1 (depth 0.01) or a rough surface (seed seed_base + index,
+    q1 = 2 pi n / 16, depth = rms height); adhesive with probability 1/2, with
+    dgamma log-uniform in [1e-4, 1e-2], preloaded to the depth and unloaded to
+    d = 0 in 8 equal steps.  A non-adhesive job is one solve at the depth."""
+    k = float(rng.uniform(-0.8, 0.8))
+    rough = bool(rng.random() < 0.5)
+    adhesive = bool(rng.random() < 0.5)
+    dgamma = float(np.exp(rng.uniform(np.log(1e-4), np.log(1e-2)))) if adhesive else 0.0
+    return {"n": int(n), "k": k, "nu": 0.3, "dgamma": dgamma, "adhesive": adhesive,
+            "profile": "rough" if rough else "paraboloid", "seed": seed_base + index}
+
+
+def job_profile(job: dict):
+    """(h, d_steps) of a job from batch_jobs / serving_requests."""
+    n = job["n"]
+    if job["profile"] == "rough":
+        h, depth = rough_self_affine(n, hurst=0.8, q1_over_q0=n / 16.0, rms_slope=0.1, seed=job["seed"])
+    else:
+        h, depth = paraboloid(n, 1.0), 0.01
+    if job["adhesive"]:
+        d_steps = depth * (1.0 - np.arange(9) / 8.0)
+    else:
+        d_steps = np.array([depth])
+    return np.ascontiguousarray(h), d_steps
+
+
+def batch_jobs(count: int = 256, seed: int = 4, sides=(128, 256, 512, 1024)) -> list:
+    """count independent solves, grid side uniform over `sides`."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    jobs = []
+    for i in range(count):
+        n = int(sides[rng.integers(len(sides))])
+        jobs.append(_job(rng, n, i, 1000))
+    return jobs
+
+
+def serving_requests(count: int = 200, seed: int = 5, rate: float = 200.0,
+                     n_min: int = 64, n_max: int = 2048) -> list:
+    """count requests with Poisson arrivals (mean rate per second): each a job
+    dict with an "arrival" time in seconds; grid side round(exp(U[ln n_min,
+    ln n_max]))."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = 0.0
+    out = []
+    for i in range(count):
+        t += float(rng.exponential(1.0 / rate))
+        n = int(round(np.exp(rng.uniform(np.log(n_min), np.log(n_max)))))
+        job = _job(rng, n, i, 5000)
+        job["arrival"] = t
+        out.append(job)
+    return out

@@ -76,3 +76,25 @@ def test_invalid_parameters_rejected_before_gpu(bem_mod):
         with pytest.raises(bem_mod.BemError) as e:
             bem_mod.Handle(*args)
         assert e.value.code == bem_mod.BEM_EINVAL
+
+
+def test_server_arguments_and_no_gpu(bem_mod):
+    import torch
+    for nworkers, budget in [(0, 1 << 30), (65, 1 << 30), (2, 1 << 20)]:
+        with pytest.raises(bem_mod.BemError) as e:
+            bem_mod.Server(nworkers, budget)
+        assert e.value.code == bem_mod.BEM_EINVAL
+    if not torch.cuda.is_available():
+        with pytest.raises(bem_mod.BemError) as e:
+            bem_mod.Server(2, 1 << 30)
+        assert e.value.code == bem_mod.BEM_ECUDA
+
+
+def test_server_footprint(bem_mod):
+    f = bem_mod.Server.footprint
+    assert f(1, 64) == 0 and f(64, 5000) == 0
+    sizes = [f(n, n) for n in (16, 64, 256, 1024, 2048)]
+    assert all(a < b for a, b in zip(sizes, sizes[1:]))
+    # at least the FP32 and FP64 CG fields and the transposed half spectrum
+    n = 1024
+    assert f(n, n) > (4 + 8) * 5 * n * n + 16 * (n + 1) * n

@@ -1,0 +1,137 @@
+"""The request server (bem_server_*): each job's result is the same alone and
+in a mix of concurrent jobs, cached spectra are reused across materials,
+admission keeps the device bytes within the budget, and a failing job reports
+its status without stopping the others."""
+import numpy as np
+import pytest
+
+import paper_1612_08395_gb300.inputs as I
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("force", "area", "contact_radius", "final_eps", "max_gap_violation", "depth",
+          "iterations", "detach_rounds", "contact_count", "status")
+
+
+def small_jobs():
+    """A mix of grids, k, materials, precisions and adhesion (paraboloid R=1 and rough)."""
+    jobs = []
+    for i, (n, k, nu, dg, prec, rough) in enumerate([
+            (64, 0.5, 0.3, 0.0, "fp64", False),
+            (64, 0.5, 0.45, 0.0, "fp64", False),        # same key as the first, other nu
+            (96, -0.4, 0.3, 1e-3, "fp32_refine", False),
+            (128, 0.3, 0.3, 0.0, "fp32_refine", True),
+            (80, 0.0, 0.25, 2e-3, "fp64", False),
+            (128, 0.3, 0.3, 1e-4, "fp32", True),
+            (48, -0.7, 0.3, 0.0, "fp32_refine", False),
+            (96, -0.4, 0.3, 1e-3, "fp32_refine", False)]):  # repeat of job 2
+        job = {"n": n, "k": k, "nu": nu, "dgamma": dg, "adhesive": dg > 0,
+               "profile": "rough" if rough else "paraboloid", "seed": 77 + i, "precision": prec}
+        jobs.append(job)
+    return jobs
+
+
+def run_alone(bem_mod, job):
+    n = job["n"]
+    h, ds = I.job_profile(job)
+    p = np.empty((n, n))
+    with bem_mod.Handle(n, n, 1.0 / n, 1.0 / n, job["k"], job["nu"]) as hd:
+        res, rc = hd.sweep(h, ds, dgamma=job["dgamma"], final_pressure=p, precision=job["precision"])
+        held = hd.info().device_bytes
+    return [r.as_dict() for r in res], p, rc, held
+
+
+def submit(srv, job):
+    n = job["n"]
+    h, ds = I.job_profile(job)
+    p = np.empty((n, n))
+    return srv.submit(n, n, 1.0 / n, 1.0 / n, job["k"], job["nu"], h, ds, dgamma=job["dgamma"],
+                      final_pressure=p, precision=job["precision"])
+
+
+def assert_same(alone, comp):
+    res_a, p_a, rc_a, _ = alone
+    assert comp["status"] == rc_a
+    for ra, rb in zip(res_a, comp["results"]):
+        rb = rb.as_dict()
+        for f in FIELDS:
+            assert ra[f] == rb[f] or (np.isnan(ra[f]) and np.isnan(rb[f])), f
+    assert np.array_equal(p_a, comp["final_pressure"])
+
+
+def test_alone_equals_mix(bem_mod):
+    jobs = small_jobs()
+    alone = [run_alone(bem_mod, j) for j in jobs]
+    with bem_mod.Server(nworkers=4, hbm_budget_bytes=4 << 30) as srv:
+        tags = [submit(srv, j) for j in jobs]
+        comps = {c["tag"]: c for c in srv.drain()}
+        assert srv.pending() == 0
+    assert sorted(comps) == sorted(tags)
+    for t, a in zip(tags, alone):
+        assert_same(a, comps[t])
+    # several jobs overlapped on the device
+    iv = sorted((c["t_start"], c["t_end"]) for c in comps.values())
+    assert any(iv[i + 1][0] < iv[i][1] for i in range(len(iv) - 1))
+
+
+def test_cached_spectrum_reused_with_new_material(bem_mod):
+    """One worker: the second job has the first one's key (grid, element size, k)
+    and another nu, so it runs on the cached handle after bem_set_material."""
+    jobs = small_jobs()[:2]
+    alone = [run_alone(bem_mod, j) for j in jobs]
+    with bem_mod.Server(nworkers=1, hbm_budget_bytes=1 << 30) as srv:
+        tags = [submit(srv, j) for j in jobs]
+        comps = {c["tag"]: c for c in srv.drain()}
+        held = srv.device_bytes()
+    for t, a in zip(tags, alone):
+        assert_same(a, comps[t])
+    assert held == alone[0][3]  # a single cached handle, reused
+
+
+def test_admission_within_budget(bem_mod):
+    n = 1024
+    budget = int(1.5 * bem_mod.Server.footprint(n, n))
+    job = {"n": n, "nu": 0.3, "dgamma": 0.0, "adhesive": False, "profile": "paraboloid",
+           "seed": 0, "precision": "fp32_refine"}
+    with bem_mod.Server(nworkers=4, hbm_budget_bytes=budget) as srv:
+        for i in range(4):  # distinct k: no handle can be shared
+            submit(srv, dict(job, k=-0.6 + 0.4 * i))
+        comps = srv.drain()
+        assert srv.device_bytes() <= budget
+        big = 2048
+        h = np.zeros((big, big))
+        with pytest.raises(bem_mod.BemError) as e:
+            srv.submit(big, big, 1 / big, 1 / big, 0.3, 0.3, h, [0.01])
+        assert e.value.code == bem_mod.BEM_ENOMEM
+    assert all(c["status"] == bem_mod.BEM_OK for c in comps)
+    iv = sorted((c["t_start"], c["t_end"]) for c in comps)
+    # only one 1024^2 job fits: the jobs ran one after another
+    assert all(iv[i + 1][0] >= iv[i][1] for i in range(len(iv) - 1))
+
+
+def test_failing_job_reports_status(bem_mod):
+    good = small_jobs()[0]
+    with bem_mod.Server(nworkers=2, hbm_budget_bytes=1 << 30) as srv:
+        t_bad = submit(srv, dict(good, nu=0.7))  # nu > 0.5: rejected by bem_create
+        t_good = submit(srv, good)
+        comps = {c["tag"]: c for c in srv.drain()}
+    assert comps[t_bad]["status"] == bem_mod.BEM_EINVAL
+    assert comps[t_good]["status"] == bem_mod.BEM_OK
+
+
+def test_batch_fp32_refine_matches_fp64(bem_mod):
+    """Jobs of the batched mix (grid sides 128 and 256 here) at FP32 + refinement
+    agree with the FP64 path: pressure relative L2 <= 1e-5 and equal contact counts."""
+    jobs = [j for j in I.batch_jobs(48, seed=4, sides=(128, 256))][:12]
+    with bem_mod.Server(nworkers=4, hbm_budget_bytes=8 << 30) as srv:
+        t32 = [submit(srv, dict(j, precision="fp32_refine")) for j in jobs]
+        t64 = [submit(srv, dict(j, precision="fp64")) for j in jobs]
+        comps = {c["tag"]: c for c in srv.drain()}
+    for a, b in zip(t32, t64):
+        ca, cb = comps[a], comps[b]
+        assert ca["status"] == bem_mod.BEM_OK and cb["status"] == bem_mod.BEM_OK
+        pa, pb = ca["final_pressure"], cb["final_pressure"]
+        nrm = np.linalg.norm(pb)
+        if nrm > 0:
+            assert np.linalg.norm(pa - pb) <= 1e-5 * nrm
+        assert ca["results"][-1].contact_count == cb["results"][-1].contact_count
