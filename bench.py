@@ -16,6 +16,13 @@ roofline    : the dominant transform pass, algorithmic bytes / its live average
 cpu_baseline: the FP64 oracle (numpy FFT mode) on a bounded sample of the same
               workload, on this host's cores
 
+batch       : (rank 0, one GPU) the seeded batch mix of independent solves
+              through the native request server at FP32 + FP64 refinement,
+              against the plain FP64 path one solve at a time; solves/s and
+              the largest final-pressure difference between the two
+serving     : the Poisson request stream (200/s) through the server and through
+              the plain FP64 path: solves/s and p50/p99 latency from arrival
+
 --impl reference times the oracle alone (rank 0) and prints its own line.
 """
 from __future__ import annotations
@@ -211,6 +218,99 @@ def cpu_oracle_sample_cached(iters):
     return res.iterations, time.perf_counter() - t0, 0.0
 
 
+def _pct(v, q):
+    return float(np.percentile(np.asarray(v), q)) if v else None
+
+
+def _job_arrays(inputs, jobs):
+    out = []
+    for j in jobs:
+        h, ds = inputs.job_profile(j)
+        out.append((h, ds, np.empty((j["n"], j["n"]))))
+    return out
+
+
+def _plain_fp64(bem, jobs, arrays, arrivals=None):
+    """One request at a time through a fresh FP64 handle (spectrum set-up included),
+    in order; a request starts at its arrival time or when the previous one ends."""
+    import torch
+    lat, t0 = [], time.perf_counter()
+    iters = 0
+    for i, (j, (h, ds, p)) in enumerate(zip(jobs, arrays)):
+        if arrivals is not None:
+            while time.perf_counter() - t0 < arrivals[i]:
+                time.sleep(1e-4)
+        n = j["n"]
+        with bem.Handle(n, n, 1.0 / n, 1.0 / n, j["k"], j["nu"]) as hd:
+            res, rc = hd.sweep(h, ds, dgamma=j["dgamma"], final_pressure=p, precision="fp64")
+        torch.cuda.synchronize()
+        iters += sum(r.iterations for r in res)
+        lat.append(time.perf_counter() - t0 - (arrivals[i] if arrivals is not None else 0.0))
+    return time.perf_counter() - t0, lat, iters
+
+
+def _served(bem, jobs, arrays, workers, budget, arrivals=None, precision="fp32_refine"):
+    """All requests through the native server; with arrival times each is
+    submitted when it arrives (Poisson stream), else all at once (a batch)."""
+    comps, sub_late = [], {}
+    with bem.Server(nworkers=workers, hbm_budget_bytes=budget) as srv:
+        t0 = time.perf_counter()
+        for i, (j, (h, ds, p)) in enumerate(zip(jobs, arrays)):
+            if arrivals is not None:
+                while time.perf_counter() - t0 < arrivals[i]:
+                    comps += srv.poll(wait_ms=0)
+                    time.sleep(1e-4)
+            n = j["n"]
+            tag = srv.submit(n, n, 1.0 / n, 1.0 / n, j["k"], j["nu"], h, ds, dgamma=j["dgamma"],
+                             final_pressure=p, precision=precision)
+            sub_late[tag] = (time.perf_counter() - t0 - (arrivals[i] if arrivals is not None else 0.0), i)
+        comps += srv.drain(1800.0)
+        el = time.perf_counter() - t0
+    lat = [c["t_end"] - c["t_submit"] + sub_late[c["tag"]][0] for c in comps]
+    bad = [c["status"] for c in comps if c["status"] != 0]
+    iters = sum(sum(r.iterations for r in c["results"]) for c in comps)
+    return el, lat, iters, bad
+
+
+def batch_and_serving(bem, inputs, n_batch, n_serve, workers):
+    """Many independent solves: the seeded batch mix (grid sides 128..1024) and a
+    Poisson request stream (rate 200/s, sides 64..2048), each through the server
+    at FP32 + FP64 refinement and through the plain FP64 path one at a time."""
+    budget = 150 << 30
+    out = {}
+    if n_batch:
+        jobs = inputs.batch_jobs(256, seed=4)[:n_batch]
+        a32 = _job_arrays(inputs, jobs)
+        a64 = [(h, ds, np.empty_like(p)) for h, ds, p in a32]
+        el, _, it32, bad = _served(bem, jobs, a32, workers, budget)
+        el64, _, it64 = _plain_fp64(bem, jobs, a64)
+        rel = [float(np.linalg.norm(x[2] - y[2]) / np.linalg.norm(y[2])) for x, y in zip(a32, a64)
+               if np.linalg.norm(y[2]) > 0]
+        out["batch"] = {
+            "workload": f"first {n_batch} of 256 seeded solves: side uniform in {{128,256,512,1024}}, "
+                        "k~U[-0.8,0.8], nu=0.3, paraboloid or rough, half adhesive (9-step unload)",
+            "solves": n_batch, "solves_per_s": n_batch / el, "cg_iterations_per_s": it32 / el,
+            "precision": "fp32_refine", "workers": workers, "failed": bad,
+            "plain_fp64": {"solves_per_s": n_batch / el64, "cg_iterations_per_s": it64 / el64},
+            "speedup_vs_plain_fp64": el64 / el,
+            "final_pressure_rel_l2_vs_fp64_max": max(rel) if rel else None}
+    if n_serve:
+        reqs = inputs.serving_requests(n_serve, seed=5)
+        arr = [r["arrival"] for r in reqs]
+        a32 = _job_arrays(inputs, reqs)
+        el, lat, it32, bad = _served(bem, reqs, a32, workers, budget, arrivals=arr)
+        el64, lat64, _ = _plain_fp64(bem, reqs, a32, arrivals=arr)
+        out["serving"] = {
+            "workload": f"{n_serve} requests, Poisson arrivals at 200/s (seed 5), side "
+                        "round(exp(U[ln 64, ln 2048])), k~U[-0.8,0.8], half adhesive; HBM budget 150 GB",
+            "requests": n_serve, "solves_per_s": n_serve / el, "p50_ms": 1e3 * _pct(lat, 50),
+            "p99_ms": 1e3 * _pct(lat, 99), "precision": "fp32_refine", "workers": workers,
+            "failed": bad, "latency": "completion minus arrival",
+            "plain_fp64": {"solves_per_s": n_serve / el64, "p50_ms": 1e3 * _pct(lat64, 50),
+                           "p99_ms": 1e3 * _pct(lat64, 99)}}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -222,6 +322,11 @@ def main():
     ap.add_argument("--sweep-steps", type=int, default=NSTEPS,
                     help="unloading steps per sweep (400 = the workload; fewer only for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch-jobs", type=int, default=64,
+                    help="solves of the batch mix to time (256 = the whole mix; 0 = skip)")
+    ap.add_argument("--serve-requests", type=int, default=32,
+                    help="requests of the Poisson stream to serve (0 = skip)")
+    ap.add_argument("--workers", type=int, default=8, help="server worker streams")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -354,9 +459,12 @@ def main():
         line["cpu_baseline"] = {"value": it / el, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": "3 Polonsky-Keer CG iterations of the 2048^2 preload solve "
                                           "(oracle FFT mode, numpy pocketfft FP64, single thread)"}
+    h.close()
+    del l2_flush
+    if rank == 0 and world == 1 and (args.batch_jobs or args.serve_requests):
+        line.update(batch_and_serving(bem, inputs, args.batch_jobs, args.serve_requests, args.workers))
     if rank == 0:
         print(json.dumps(line), flush=True)
-    h.close()
     if world > 1:
         dist.destroy_process_group()
     return 0

@@ -107,7 +107,8 @@ extern "C" int bem_convolve_noalloc(const double* khat, int Nx, int Ny, double c
   if (g_off + sizeof(int) * g_ints > kScratchBytes)
     return bem::set_error(BEM_EINVAL, "bem_convolve_noalloc: grid needs more than the 2 MiB static scratch");
 
-  // launch geometry: the same rules as the handle's FP64 plan
+  // launch geometry of the plain FP64 passes (rows per CTA as a handle's plan
+  // chooses them before it spreads small grids over more CTAs)
   bem::Plan pl{};
   pl.nx = Nx; pl.ny = Ny; pl.px = px; pl.py = py; pl.M = M;
   const int tr = M / 8;

@@ -81,7 +81,13 @@ template <typename T> struct PrecFields {
 int ilog2(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
 int pow2_at_least(int v) { int p = 1; while (p < v) p <<= 1; return p; }
 
-Plan make_plan(int nx, int ny, int px, int py, int esize) {
+// Small grids: fewer rows (columns) per CTA until a pass has about two CTAs
+// per SM, keeping at least two warps per CTA -- otherwise a 128^2 grid runs
+// its passes on a handful of SMs and every CG iteration is latency-bound.
+constexpr int kMinThreads = 64;
+constexpr int kCtasPerSm = 2;
+
+Plan make_plan(int nx, int ny, int px, int py, int esize, int nsm) {
   Plan pl{};
   pl.nx = nx; pl.ny = ny; pl.px = px; pl.py = py;
   pl.M = px / 2;
@@ -93,6 +99,7 @@ Plan make_plan(int nx, int ny, int px, int py, int esize) {
   if (nb < 1) nb = 1;
   while (nb > 1 && nb * tr > BEM_MAX_THREADS_A) nb >>= 1;
   while (nb > 1 && (size_t)nb * (pl.M + 32) * 2 * esize > 128 * 1024) nb >>= 1;
+  while (nb > 1 && (nb / 2) * tr >= kMinThreads && (ny + nb - 1) / nb < kCtasPerSm * nsm) nb >>= 1;
   pl.nbA = nb;
   pl.lognbA = ilog2(nb);
   pl.gA = make_geo(logM, nb, esize);
@@ -104,11 +111,13 @@ Plan make_plan(int nx, int ny, int px, int py, int esize) {
   int nbb = 256 / tb;
   if (nbb < 1) nbb = 1;
   while (nbb > 1 && (size_t)nbb * (py + 32) * 2 * esize > 128 * 1024) nbb >>= 1;
+  while (nbb > 1 && (nbb / 2) * tb >= kMinThreads && (pl.M + nbb) / nbb < kCtasPerSm * nsm) nbb >>= 1;
   pl.nbB = nbb;
   pl.gB = make_geo(logPy, nbb, esize);
   pl.threadsB = nbb * tb;
   pl.gridB = (pl.M + 1 + nbb - 1) / nbb;
   pl.smemB = (size_t)nbb * pl.gB.rs * 2 * esize;
+  pl.nsm = nsm;
   return pl;
 }
 
@@ -471,7 +480,7 @@ int max_abs_on_set(bem_ctx* h, const double* x, double* out) {
 // the FP32 fixed-set CG, and adds dp.  Non-adhesive: S = {p > 0} U {g < 0} and
 // p is projected onto p >= 0 after the update; adhesive: S is held and tension
 // is allowed.  Stops when max_S |g64| <= tol64 * max_S |h - d|.
-int refine(bem_ctx* h, double d, bool adhesive, int sweeps, double tol64, StepOut* so) {
+int refine(bem_ctx* h, double d, bool adhesive, int sweeps, double tol64, double tol32, StepOut* so) {
   const size_t n = (size_t)h->nx * h->ny;
   for (int s = 0; s < sweeps; ++s) {
     CKR(gap64(h, d));
@@ -486,7 +495,7 @@ int refine(bem_ctx* h, double d, bool adhesive, int sweeps, double tol64, StepOu
     CK(cudaMemsetAsync(h->f32.p, 0, n * sizeof(float), h->stream));
     CK(cudaMemsetAsync(h->f32.t, 0, n * sizeof(float), h->stream));
     StepOut cg;
-    CKR(run_fixed_cg<float>(h, 1e-6, 2000, 0.0, &cg));
+    CKR(run_fixed_cg<float>(h, tol32, 2000, 0.0, &cg));
     so->iterations += cg.iterations;
     if (h->sc_host->status == SC_NUMERIC) { so->status = BEM_ENUMERIC; break; }
     launch_refine_apply(h->io64, h->f32.p, res, h->S, adhesive ? 0 : 1, n, h->stream);
@@ -555,13 +564,12 @@ extern "C" int bem_create(int Nx, int Ny, double dx, double dy, double k, double
   h->A = alpha * (1.0 - nu * nu) * pow(c0, k) / E0;  // Eq. 12
   h->px = pow2_at_least(2 * Nx < 32 ? 32 : 2 * Nx);
   h->py = pow2_at_least(2 * Ny < 32 ? 32 : 2 * Ny);
-  h->plan32 = make_plan(Nx, Ny, h->px, h->py, 4);
-  h->plan64 = make_plan(Nx, Ny, h->px, h->py, 8);
   {
     int nsm = 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || nsm < 1)
       return cleanup(fail(BEM_ECUDA, "cannot query the SM count"));
-    h->plan32.nsm = h->plan64.nsm = nsm;
+    h->plan32 = make_plan(Nx, Ny, h->px, h->py, 4, nsm);
+    h->plan64 = make_plan(Nx, Ny, h->px, h->py, 8, nsm);
   }
   const int M = h->px / 2, hyq = h->py / 2 + 1;
   const size_t n = (size_t)Nx * Ny;
@@ -789,7 +797,7 @@ int step_nonadhesive(bem_ctx* h, const SolveCfg& cfg, double d, bool warm, bem_r
     launch_convert_out<float>(h->f32.p, h->io64, n, h->stream);
     h->launches += 1;
     if (cfg.precision == BEM_PREC_FP32_REFINE) {
-      CKR(refine(h, d, false, cfg.sweeps, 1e-13, &so));
+      CKR(refine(h, d, false, cfg.sweeps, 1e-13, cfg.tol, &so));
       CKR(gap64(h, d));
       CKR(collect<double>(h, h->io64, h->f64.g, 0, r));
       // keep the FP32 warm start in step with the refined pressure
@@ -821,7 +829,7 @@ int step_adhesive_t(bem_ctx* h, const SolveCfg& cfg, double d, double pcrit, bem
     CKR(run_fixed_cg<T>(h, tol, cfg.max_iter, pcrit, &so));
     if (cfg.precision == BEM_PREC_FP32_REFINE) {
       launch_convert_out<float>(h->f32.p, h->io64, n, h->stream);
-      CKR(refine(h, d, true, cfg.sweeps, 1e-13, &so));
+      CKR(refine(h, d, true, cfg.sweeps, 1e-13, cfg.tol, &so));
       launch_to_f32(h->io64, h->f32.p, n, h->stream);
       launch_offset<float>(h->h64, d, h->f32.c, n, h->stream);
       h->launches += 3;
