@@ -49,6 +49,9 @@ struct Scalars {
   int max_iter, iter, done, status, have_tau, it_min;
   int nA, pad1;   // CTAs of the last pass A launch (its partials feed pass C)
   unsigned int cnt_a, cnt_c, cnt_e, cnt_r;  // last-block arrival counters
+  // Sticky device error bits (kept across solves: init_scalars does not copy
+  // this member); 1 = a kernel gave up waiting for its own asynchronous copies.
+  unsigned int kerr, pad2;
 };
 
 enum { SC_OK = 0, SC_NOCONV = 1, SC_NUMERIC = 2, SC_STALL = 3 };
@@ -107,6 +110,7 @@ struct PassArgs {
   double* partA;        // per-CTA partials, 4 per CTA
   double* partC;
   Scalars* sc;
+  unsigned int* kerr;   // sticky error word (may be null: errors then go unreported)
 };
 
 template <typename T> void launch_pass_a(const PassArgs<T>& a, int mode, cudaStream_t s);

@@ -185,6 +185,44 @@ __device__ __forceinline__ void pro_gather(const PassArgs<T>& a, size_t i, PIn<T
   }
 }
 
+template <typename T> struct V2T;
+template <> struct V2T<float> { using type = float2; };
+template <> struct V2T<double> { using type = double2; };
+template <typename T> using V2 = typename V2T<T>::type;
+
+// The field a prologue mode rewrites with the transform input (null: none).
+template <typename T, int MODE>
+__device__ __forceinline__ T* pro_out(const PassArgs<T>& a) {
+  if (MODE == A_PK_P) return a.f.p;
+  if (MODE == A_PK_T || MODE == A_CG_T) return a.f.t;
+  return nullptr;
+}
+
+// Transform input of one element with the CG work of the mode (the value the
+// mode also stores back into pro_out), without the store.
+template <typename T, int MODE>
+__device__ __forceinline__ T pro_value(const PIn<T>& x, bool upd, T tau, T beta, T* acc) {
+  if (MODE == A_PLAIN) {
+    return x.p;
+  } else if (MODE == A_PK_P) {
+    T q = x.p;
+    if (upd) {
+      if (x.p > (T)0) {
+        q = x.p - tau * x.t;
+        q = q > (T)0 ? q : (T)0;
+      }
+      if (q == (T)0 && x.g < (T)0) { q = -tau * x.g; acc[2] += (T)1; }
+      acc[0] += tabs(q - x.p);
+    }
+    acc[1] += q;
+    return q;
+  } else if (MODE == A_PK_T) {
+    return x.p > (T)0 ? x.g + beta * x.t : (T)0;
+  } else {  // A_CG_T
+    return x.s ? x.g + beta * x.t : (T)0;
+  }
+}
+
 template <typename T, int MODE>
 __device__ __forceinline__ T pro_apply(const PassArgs<T>& a, size_t i, const PIn<T>& x, bool upd,
                                        T tau, T beta, T* acc) {
@@ -343,7 +381,8 @@ __global__ void BEM_ROW_BOUNDS(LOGL) k_pass_a(PassArgs<T> a) {
 // ---------------------------------------------------------------------------
 // Persistent pass A: each CTA loops over row groups (nbA rows each) and, while
 // it transforms one group, its prologue fields for the next group stream into
-// shared memory with cp.async.  Used when rows are multiples of 16 elements.
+// shared memory as bulk copies (one per field row).  Used when rows are
+// multiples of 16 elements and the fields are 16-byte aligned.
 template <int MODE> struct ProStage {
   static constexpr int nT = (MODE == A_PK_P || MODE == A_PK_T) ? 3 : (MODE == A_CG_T ? 2 : (MODE == A_PLAIN ? 1 : 0));
   static constexpr bool S = MODE == A_CG_T;
@@ -358,28 +397,47 @@ __device__ __forceinline__ const T* pro_field(const PassArgs<T>& a, int f) {
   if (MODE == A_CG_T) return f == 0 ? a.f.t : a.f.g;
   return f == 0 ? a.f.p : (f == 1 ? a.f.t : a.f.g);
 }
+// Thread 0 stages the prologue fields of rows row0 .. row0+rows-1 into shared
+// memory: one bulk copy per field row, completing on `bar` (16-byte aligned
+// rows: the persistent launch requires nx % 16 == 0 and aligned fields).
 template <typename T, int MODE>
 __device__ __forceinline__ void pro_prefetch(const PassArgs<T>& a, T* st, uint8_t* ss, int row0, int rows,
-                                             int nx, int nb) {
-  const int cpr = nx * (int)sizeof(T) / 16;
+                                             int nx, int nb, unsigned long long* bar) {
+  if (threadIdx.x != 0) return;
+  const unsigned rb = (unsigned)(nx * (int)sizeof(T));
+  fence_proxy_async_smem();
+  mbar_expect_tx(bar, (unsigned)rows * (ProStage<MODE>::nT * rb + (ProStage<MODE>::S ? (unsigned)nx : 0u)));
 #pragma unroll
   for (int f = 0; f < ProStage<MODE>::nT; ++f) {
     const T* src = pro_field<T, MODE>(a, f);
-    for (int q = threadIdx.x; q < cpr * rows; q += blockDim.x) {
-      const int bb = q / cpr, ch = q - bb * cpr;
-      cp_async16(reinterpret_cast<char*>(st + ((size_t)f * nb + bb) * nx) + 16 * ch,
-                 reinterpret_cast<const char*>(src + (size_t)(row0 + bb) * nx) + 16 * ch);
-    }
+    for (int bb = 0; bb < rows; ++bb)
+      bulk_g2s(st + ((size_t)f * nb + bb) * nx, src + (size_t)(row0 + bb) * nx, rb, bar);
   }
   if (ProStage<MODE>::S) {
-    const int cps = nx / 16;
-    for (int q = threadIdx.x; q < cps * rows; q += blockDim.x) {
-      const int bb = q / cps, ch = q - bb * cps;
-      cp_async16(ss + (size_t)bb * nx + 16 * ch, a.f.S + (size_t)(row0 + bb) * nx + 16 * ch);
-    }
+    for (int bb = 0; bb < rows; ++bb)
+      bulk_g2s(ss + (size_t)bb * nx, a.f.S + (size_t)(row0 + bb) * nx, (unsigned)nx, bar);
   }
-  cp_async_commit();
 }
+// Both elements of an even column pair (col, col+1) from the staging area.
+template <typename T, int MODE>
+__device__ __forceinline__ void pro_gather_pair_staged(const T* st, const uint8_t* ss, int b, int col, int nx,
+                                                       int nb, PIn<T>& x0, PIn<T>& x1) {
+  const size_t j = (size_t)b * nx + col, plane = (size_t)nb * nx;
+  const V2<T>* s2 = reinterpret_cast<const V2<T>*>(st + j);
+  const size_t p2 = plane / 2;
+  if (MODE == A_PLAIN) {
+    const V2<T> v = s2[0];
+    x0.p = v.x; x1.p = v.y;
+  } else if (MODE == A_CG_T) {
+    const V2<T> vt = s2[0], vg = s2[p2];
+    const uchar2 vs = *reinterpret_cast<const uchar2*>(ss + j);
+    x0.t = vt.x; x1.t = vt.y; x0.g = vg.x; x1.g = vg.y; x0.s = vs.x; x1.s = vs.y;
+  } else {
+    const V2<T> vp = s2[0], vt = s2[p2], vg = s2[2 * p2];
+    x0.p = vp.x; x1.p = vp.y; x0.t = vt.x; x1.t = vt.y; x0.g = vg.x; x1.g = vg.y;
+  }
+}
+
 template <typename T, int MODE>
 __device__ __forceinline__ void pro_gather_staged(const T* st, const uint8_t* ss, int b, int col, int nx,
                                                   int nb, PIn<T>& x) {
@@ -426,39 +484,50 @@ __global__ void BEM_ROWP_BOUNDS(LOGL) k_pass_ap(PassArgs<T> a) {
   if (MODE == A_PK_T || MODE == A_CG_T) beta = (T)sc->beta;
   if (MODE == A_PK_P && blockIdx.x == 0 && tid == 0) sc->nA = gridDim.x;
 
+  __shared__ unsigned long long bar;
+  if (tid == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  unsigned phase = 0;
   int g = blockIdx.x;
-  if (g < G) pro_prefetch<T, MODE>(a, st, ss, g * nb, min(nb, nrows - g * nb), ncols, nb);
+  if (g < G) pro_prefetch<T, MODE>(a, st, ss, g * nb, min(nb, nrows - g * nb), ncols, nb, &bar);
   for (; g < G; g += gridDim.x) {
     const int row0 = g * nb, row = row0 + b;
     const bool act = row < nrows;
     const size_t rowoff = (size_t)row * ncols;
-    cp_async_wait_all();
-    __syncthreads();
+    const bool ok = mbar_wait(&bar, phase);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) {  // the staged rows never arrived: give up together
+      if (tid == 0 && a.kerr) atomicOr(a.kerr, 1u);
+      return;
+    }
+    // ncols is a multiple of 16 here: column pairs (2n, 2n+1) are whole
     PIn<T> in[8][2];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       if (!F::first_half(e)) continue;
       const int n = F::n0(t, e);
-#pragma unroll
-      for (int h = 0; h < 2; ++h)
-        if (act && n < half && 2 * n + h < ncols)
-          pro_gather_staged<T, MODE>(st, ss, b, 2 * n + h, ncols, nb, in[e][h]);
+      if (act && n < half) pro_gather_pair_staged<T, MODE>(st, ss, b, 2 * n, ncols, nb, in[e][0], in[e][1]);
     }
     __syncthreads();  // staging consumed: refill it for the next group
     const int gn = g + gridDim.x;
-    if (gn < G) pro_prefetch<T, MODE>(a, st, ss, gn * nb, min(nb, nrows - gn * nb), ncols, nb);
+    if (gn < G) pro_prefetch<T, MODE>(a, st, ss, gn * nb, min(nb, nrows - gn * nb), ncols, nb, &bar);
     Cx v[8];
+    T* out = pro_out<T, MODE>(a);
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       v[e] = mk<T>(0, 0);
       if (!F::first_half(e)) continue;
       const int n = F::n0(t, e);
-      T xv[2] = {0, 0};
-#pragma unroll
-      for (int h = 0; h < 2; ++h)
-        if (act && n < half && 2 * n + h < ncols)
-          xv[h] = pro_apply<T, MODE>(a, rowoff + 2 * n + h, in[e][h], upd, tau, beta, acc);
-      v[e] = mk<T>(xv[0], xv[1]);
+      if (act && n < half) {
+        const T x0 = pro_value<T, MODE>(in[e][0], upd, tau, beta, acc);
+        const T x1 = pro_value<T, MODE>(in[e][1], upd, tau, beta, acc);
+        if (MODE != A_PLAIN) {
+          V2<T> o;
+          o.x = x0; o.y = x1;
+          *reinterpret_cast<V2<T>*>(out + rowoff + 2 * n) = o;
+        }
+        v[e] = mk<T>(x0, x1);
+      }
     }
     F::stage0_fwd(v, t, tw);
 #pragma unroll
@@ -490,7 +559,6 @@ __global__ void BEM_ROWP_BOUNDS(LOGL) k_pass_ap(PassArgs<T> a) {
       W[(size_t)k * a.rows_w + rw] = X;
     }
   }
-  cp_async_wait_all();
   if (MODE == A_PK_P) {
     double vv[3] = {(double)acc[0], (double)acc[1], (double)acc[2]};
     block_sum<3>(vv, red);
@@ -645,6 +713,63 @@ __device__ __forceinline__ void epi_gather_staged(const T* st, const uint8_t* ss
   else if (MODE == C_CG_R) { x.t = st[j]; x.s = ss[j]; }
   else if (MODE == C_CG_G) { x.c = st[j]; x.s = ss[j]; }
   else if (MODE == C_GAP) { x.c = st[j]; }
+}
+
+// The field an epilogue mode writes (null: none) and the value it writes.
+template <typename T, int MODE>
+__device__ __forceinline__ T* epi_out(const PassArgs<T>& a) {
+  if (MODE == C_PLAIN) return a.f.dst;
+  if (MODE == C_PK_G || MODE == C_CG_G || MODE == C_GAP) return a.f.g;
+  if (MODE == C_CG_R) return a.f.r;
+  return nullptr;
+}
+template <typename T, int MODE>
+__device__ __forceinline__ T epi_value(T u, const EIn<T>& x, T* acc) {
+  if (MODE == C_PLAIN) {
+    return u;
+  } else if (MODE == C_PK_G) {
+    const T gv = u + x.c;
+    if (x.p > (T)0) { acc[0] += gv * gv; acc[1] += (T)1; }
+    return gv;
+  } else if (MODE == C_PK_R) {
+    if (x.p > (T)0) { acc[0] += x.g * x.t; acc[1] += u * x.t; }
+    return (T)0;
+  } else if (MODE == C_CG_R) {
+    const T rv = x.s ? u : (T)0;
+    acc[0] += rv * x.t;
+    return rv;
+  } else if (MODE == C_CG_G) {
+    if (x.s) {
+      const T gv = u + x.c;
+      acc[0] += gv * gv;
+      acc[1] += x.c * x.c;
+      return gv;
+    }
+    return (T)0;
+  } else {  // C_GAP
+    return u + x.c;
+  }
+}
+template <typename T, int MODE>
+__device__ __forceinline__ void epi_gather_pair_staged(const T* st, const uint8_t* ss, int b, int col, int nx,
+                                                       int nb, EIn<T>& x0, EIn<T>& x1) {
+  const size_t j = (size_t)b * nx + col, plane = (size_t)nb * nx;
+  const V2<T>* s2 = reinterpret_cast<const V2<T>*>(st + j);
+  if (MODE == C_PK_G) {
+    const V2<T> vc = s2[0], vp = s2[plane / 2];
+    x0.c = vc.x; x1.c = vc.y; x0.p = vp.x; x1.p = vp.y;
+  } else if (MODE == C_CG_R) {
+    const V2<T> vt = s2[0];
+    const uchar2 vs = *reinterpret_cast<const uchar2*>(ss + j);
+    x0.t = vt.x; x1.t = vt.y; x0.s = vs.x; x1.s = vs.y;
+  } else if (MODE == C_CG_G) {
+    const V2<T> vc = s2[0];
+    const uchar2 vs = *reinterpret_cast<const uchar2*>(ss + j);
+    x0.c = vc.x; x1.c = vc.y; x0.s = vs.x; x1.s = vs.y;
+  } else if (MODE == C_GAP) {
+    const V2<T> vc = s2[0];
+    x0.c = vc.x; x1.c = vc.y;
+  }
 }
 
 template <typename T, int MODE>
@@ -899,9 +1024,9 @@ __global__ void BEM_ROW_BOUNDS(LOGL) k_pass_c(PassArgs<T> a) {
 
 // ---------------------------------------------------------------------------
 // Persistent pass C: each CTA loops over row groups; the strided W rows of the
-// next group and the epilogue fields stream into shared memory with cp.async
-// (two commit groups per row group, waited for separately) while the current
-// group is transformed.  Used when rows are multiples of 16 elements.
+// next group stream into shared memory with cp.async and its epilogue fields
+// as bulk copies (one per field row, on an mbarrier) while the current group
+// is transformed.  Used when rows are multiples of 16 elements.
 template <typename T, int MODE, int LOGL>
 __global__ void BEM_ROWP_BOUNDS(LOGL) k_pass_cp(PassArgs<T> a) {
   using Cx = C<T>;
@@ -934,42 +1059,55 @@ __global__ void BEM_ROWP_BOUNDS(LOGL) k_pass_cp(PassArgs<T> a) {
 
   auto prefetch_w = [&](int gg) {
     const int r0 = gg * nb, rows = min(nb, ny - r0);
-    for (int q = tid; q < (M + 1) << lognb; q += nthr) {
-      const int k = q >> lognb, bb = q & (nb - 1);
-      if (bb < rows) cp_async_cx<Cx>(wst + q, W + (size_t)k * a.rows_w + r0 + bb);
+    if (sizeof(Cx) == 8 && nb >= 2 && rows == nb && (a.rows_w & 1) == 0) {
+      // FP32 and an even number of full rows: 16-byte chunks of two rows
+      const int lh = lognb - 1;
+      for (int q = tid; q < (M + 1) << lh; q += nthr) {
+        const int k = q >> lh, j = q & ((1 << lh) - 1);
+        cp_async16(wst + (k << lognb) + 2 * j, W + (size_t)k * a.rows_w + r0 + 2 * j);
+      }
+    } else {
+      for (int q = tid; q < (M + 1) << lognb; q += nthr) {
+        const int k = q >> lognb, bb = q & (nb - 1);
+        if (bb < rows) cp_async_cx<Cx>(wst + q, W + (size_t)k * a.rows_w + r0 + bb);
+      }
     }
     cp_async_commit();
   };
+  // epilogue fields: thread 0 issues one bulk copy per field row, completing on ebar
+  __shared__ unsigned long long ebar;
+  if (tid == 0) mbar_init(&ebar, 1);
+  __syncthreads();
+  unsigned ephase = 0;
   auto prefetch_e = [&](int gg) {
+    if (tid != 0) return;
     const int r0 = gg * nb, rows = min(nb, ny - r0);
-    const int cpr = nx * (int)sizeof(T) / 16;
+    const unsigned rb = (unsigned)(nx * (int)sizeof(T));
+    fence_proxy_async_smem();
+    mbar_expect_tx(&ebar, (unsigned)rows * (EpiStage<MODE>::nT * rb + (EpiStage<MODE>::S ? (unsigned)nx : 0u)));
 #pragma unroll
     for (int f = 0; f < EpiStage<MODE>::nT; ++f) {
       const T* src = (MODE == C_PK_G) ? (f == 0 ? a.f.c : a.f.p) : (MODE == C_CG_R ? a.f.t : a.f.c);
-      for (int q = tid; q < cpr * rows; q += nthr) {
-        const int bb = q / cpr, ch = q - bb * cpr;
-        cp_async16(reinterpret_cast<char*>(st + ((size_t)f * nb + bb) * nx) + 16 * ch,
-                   reinterpret_cast<const char*>(src + (size_t)(r0 + bb) * nx) + 16 * ch);
-      }
+      for (int bb = 0; bb < rows; ++bb)
+        bulk_g2s(st + ((size_t)f * nb + bb) * nx, src + (size_t)(r0 + bb) * nx, rb, &ebar);
     }
     if (EpiStage<MODE>::S) {
-      const int cps = nx / 16;
-      for (int q = tid; q < cps * rows; q += nthr) {
-        const int bb = q / cps, ch = q - bb * cps;
-        cp_async16(ss + (size_t)bb * nx + 16 * ch, a.f.S + (size_t)(r0 + bb) * nx + 16 * ch);
-      }
+      for (int bb = 0; bb < rows; ++bb)
+        bulk_g2s(ss + (size_t)bb * nx, a.f.S + (size_t)(r0 + bb) * nx, (unsigned)nx, &ebar);
     }
-    cp_async_commit();
   };
 
   const T us = (T)a.uscale;
   T acc[3] = {0, 0, 0};
   const int half = (nx + 1) >> 1;
   int g = blockIdx.x;
-  if (g < G) { prefetch_w(g); prefetch_e(g); }
+  if (g < G) {
+    prefetch_w(g);
+    if (EpiStage<MODE>::any) prefetch_e(g);
+  }
   for (; g < G; g += gridDim.x) {
     const int row0 = g * nb;
-    cp_async_wait_1();  // W of this group (its epilogue fields may still be in flight)
+    cp_async_wait_all();  // W of this group
     __syncthreads();
     // rebuild the packed half-length spectrum from the staged W rows
 #pragma unroll 2
@@ -998,41 +1136,53 @@ __global__ void BEM_ROWP_BOUNDS(LOGL) k_pass_cp(PassArgs<T> a) {
       F::dit(buf, t, ls, tw);
       __syncthreads();
     }
-    if (gn < G) cp_async_wait_1(); else cp_async_wait_all();  // epilogue fields of this group
-    __syncthreads();
+    if (EpiStage<MODE>::any) {  // epilogue fields of this group
+      const bool ok = mbar_wait(&ebar, ephase);
+      ephase ^= 1u;
+      if (__syncthreads_or(!ok)) {  // they never arrived: give up together
+        cp_async_wait_all();
+        if (tid == 0 && a.kerr) atomicOr(a.kerr, 1u);
+        return;
+      }
+    }
     const int row = row0 + b;
     const bool act = row < ny;
     const size_t rowoff = (size_t)row * nx;
+    // nx is a multiple of 16 here: column pairs (2n, 2n+1) are whole
     EIn<T> ein[8][2];
     if (MODE != C_PLAIN) {
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         if (!F::first_half(e)) continue;
         const int n = F::n0(t, e);
-#pragma unroll
-        for (int h = 0; h < 2; ++h)
-          if (act && n < half && 2 * n + h < nx) {
-            if (EpiStage<MODE>::any) epi_gather_staged<T, MODE>(st, ss, b, 2 * n + h, nx, nb, ein[e][h]);
-            else epi_gather<T, MODE>(a, rowoff + 2 * n + h, ein[e][h]);
+        if (act && n < half) {
+          if (EpiStage<MODE>::any) {
+            epi_gather_pair_staged<T, MODE>(st, ss, b, 2 * n, nx, nb, ein[e][0], ein[e][1]);
+          } else {
+            epi_gather<T, MODE>(a, rowoff + 2 * n, ein[e][0]);
+            epi_gather<T, MODE>(a, rowoff + 2 * n + 1, ein[e][1]);
           }
+        }
       }
     }
     Cx v[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) v[e] = buf[F::ix0(t, e)];
     F::stage0_inv(v, t, tw);
+    T* out = epi_out<T, MODE>(a);
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       if (!F::first_half(e)) continue;
       const int n = F::n0(t, e);
-#pragma unroll
-      for (int h = 0; h < 2; ++h)
-        if (act && n < half && 2 * n + h < nx)
-          epi_apply<T, MODE>(a, rowoff + 2 * n + h, us * (h ? v[e].y : v[e].x), ein[e][h], acc);
+      if (act && n < half) {
+        V2<T> o;
+        o.x = epi_value<T, MODE>(us * v[e].x, ein[e][0], acc);
+        o.y = epi_value<T, MODE>(us * v[e].y, ein[e][1], acc);
+        if (MODE != C_PK_R) *reinterpret_cast<V2<T>*>(out + rowoff + 2 * n) = o;
+      }
     }
     __syncthreads();  // epilogue staging and transform rows consumed
     if (gn < G && EpiStage<MODE>::any) prefetch_e(gn);
-    else if (gn < G) cp_async_commit();  // keep the two-groups-per-iteration accounting
   }
   cp_async_wait_all();
   if (MODE == C_PLAIN || MODE == C_GAP) return;
@@ -1259,11 +1409,25 @@ int resident_ctas(K kernel, int threads, size_t smem) {
 #define BEM_PERSISTENT 1
 #endif
 
+inline bool aligned16(const void* p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+// The persistent row passes stage whole field rows with 16-byte bulk copies.
+template <typename T, int MODE>
+bool pro_fields_aligned(const PassArgs<T>& a) {
+  if (MODE == A_PLAIN) return aligned16(a.f.src);
+  return aligned16(a.f.p) && aligned16(a.f.t) && aligned16(a.f.g) && aligned16(a.f.S);
+}
+template <typename T>
+bool epi_fields_aligned(const PassArgs<T>& a) {
+  return aligned16(a.f.c) && aligned16(a.f.p) && aligned16(a.f.t) && aligned16(a.f.S) && aligned16(a.W) &&
+         aligned16(a.f.dst) && aligned16(a.f.g) && aligned16(a.f.r);
+}
+
 template <typename T, int MODE>
 void launch_a_mode(const PassArgs<T>& a, cudaStream_t s) {
   const dim3 block(a.pl.threadsA);
   const int groups = (a.nrows_in + a.pl.nbA - 1) / a.pl.nbA;
-  if (BEM_PERSISTENT && MODE != A_TORUS && (a.ncols_in & 15) == 0) {
+  if (BEM_PERSISTENT && MODE != A_TORUS && (a.ncols_in & 15) == 0 && pro_fields_aligned<T, MODE>(a)) {
     const size_t smem = ((a.pl.smemA + 15) & ~(size_t)15) + pro_stage_bytes<T, MODE>(a.pl.nbA, a.ncols_in);
     switch (a.pl.gA.logL) {
 #define BEM_CASE(LG)                                                                        \
@@ -1297,7 +1461,7 @@ template <typename T, int MODE>
 void launch_c_mode(const PassArgs<T>& a, cudaStream_t s) {
   const dim3 block(a.pl.threadsA);
   const int groups = a.pl.gridA;
-  if (BEM_PERSISTENT && (a.pl.nx & 15) == 0) {
+  if (BEM_PERSISTENT && (a.pl.nx & 15) == 0 && epi_fields_aligned<T>(a)) {
     const size_t smem = ((a.pl.smemC + 15) & ~(size_t)15) +
                         ((sizeof(C<T>) * (size_t)(a.pl.M + 1) * a.pl.nbA + 15) & ~(size_t)15) +
                         epi_stage_bytes<T, MODE>(a.pl.nbA, a.pl.nx);

@@ -3,6 +3,7 @@
 // of captured CUDA graphs, the adhesive detach loop, the FP64 refinement
 // sweep, load-unload sweeps, and the C ABI of include/bem.h.
 #include <math.h>
+#include <stddef.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -225,6 +226,7 @@ PassArgs<T> make_args(bem_ctx* h) {
   a.partA = h->part;
   a.partC = h->partC;
   a.sc = h->sc;
+  a.kerr = &h->sc->kerr;
   return a;
 }
 
@@ -251,9 +253,15 @@ int download(bem_ctx* h, double* dst, const double* src, size_t n) {
   return BEM_OK;
 }
 
+int device_error(bem_ctx* h) {
+  return fail(BEM_ETIMEOUT, "a kernel gave up waiting for its own asynchronous copies (error bits %#x)",
+              h->sc_host->kerr);
+}
+
 int read_scalars(bem_ctx* h) {
   CK(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  if (h->sc_host->kerr) return device_error(h);
   return BEM_OK;
 }
 
@@ -265,8 +273,10 @@ int init_scalars(bem_ctx* h, double tol, int max_iter, double pcrit) {
   s.delta = 0.0;
   s.bnorm = 1.0;
   s.pcrit = pcrit;
+  s.kerr = h->sc_host->kerr;
   *h->sc_host = s;
-  CK(cudaMemcpyAsync(h->sc, h->sc_host, sizeof(Scalars), cudaMemcpyHostToDevice, h->stream));
+  // every member but the sticky error word
+  CK(cudaMemcpyAsync(h->sc, h->sc_host, offsetof(Scalars, kerr), cudaMemcpyHostToDevice, h->stream));
   // the host copy is reused for reads; make sure the upload has consumed it
   CK(cudaStreamSynchronize(h->stream));
   return BEM_OK;
@@ -440,7 +450,9 @@ int collect(bem_ctx* h, const T* p, const T* g, int use_set, bem_result* r) {
                   h->stream);
   h->launches += 1;
   CK(cudaMemcpyAsync(h->stats_host, h->stats, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(&h->sc_host->kerr, &h->sc->kerr, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  if (h->sc_host->kerr) return device_error(h);
   const double cell = h->dx * h->dy;
   r->force = cell * h->stats_host[0];
   r->contact_count = (int)h->stats_host[1];
@@ -598,6 +610,7 @@ extern "C" int bem_create(int Nx, int Ny, double dx, double dy, double k, double
   if (cudaMallocHost((void**)&h->sc_host, sizeof(Scalars)) != cudaSuccess ||
       cudaMallocHost((void**)&h->stats_host, 8 * sizeof(double)) != cudaSuccess)
     return cleanup(fail(BEM_ENOMEM, "pinned allocation failed"));
+  memset(h->sc_host, 0, sizeof(Scalars));
   if (cudaMemsetAsync(h->sc, 0, sizeof(Scalars), h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->stats, 0, sizeof(double) * (8 + 4 * (size_t)h->stats_ngrid + 8), h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->S, 0, n, h->stream) != cudaSuccess)
