@@ -11,6 +11,40 @@ template <> struct cplx_t<float> { using type = float2; };
 template <> struct cplx_t<double> { using type = double2; };
 template <typename T> using C = typename cplx_t<T>::type;
 
+// ---------------------------------------------------------------------------
+// Packed FP32 pairs: one instruction for both components (Blackwell f32x2,
+// IEEE round-to-nearest like the scalar instructions).
+__device__ __forceinline__ float2 padd(float2 a, float2 b) {
+  float2 r;
+  asm("{\n .reg .b64 ra, rb, rc;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+      " add.rn.f32x2 rc, ra, rb;\n mov.b64 {%0, %1}, rc;\n}"
+      : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+__device__ __forceinline__ float2 psub(float2 a, float2 b) {
+  float2 r;
+  asm("{\n .reg .b64 ra, rb, rc;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+      " sub.rn.f32x2 rc, ra, rb;\n mov.b64 {%0, %1}, rc;\n}"
+      : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+// a * (s, s) + c
+__device__ __forceinline__ float2 pfma_s(float2 a, float sc, float2 c) {
+  float2 r;
+  asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %4};\n"
+      " mov.b64 rc, {%5, %6};\n fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(sc), "f"(c.x), "f"(c.y));
+  return r;
+}
+// a * (s, s)
+__device__ __forceinline__ float2 pmul_s(float2 a, float sc) {
+  float2 r;
+  asm("{\n .reg .b64 ra, rb, rc;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %4};\n"
+      " mul.rn.f32x2 rc, ra, rb;\n mov.b64 {%0, %1}, rc;\n}"
+      : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(sc));
+  return r;
+}
+
 template <typename T> __device__ __forceinline__ C<T> mk(T re, T im) { C<T> c; c.x = re; c.y = im; return c; }
 template <typename T> __device__ __forceinline__ C<T> add(C<T> a, C<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
 template <typename T> __device__ __forceinline__ C<T> sub(C<T> a, C<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
@@ -18,7 +52,10 @@ template <typename T> __device__ __forceinline__ C<T> mul(C<T> a, C<T> b) {
   return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 template <typename T> __device__ __forceinline__ C<T> conj(C<T> a) { return mk<T>(a.x, -a.y); }
-template <typename T> __device__ __forceinline__ C<T> scale(C<T> a, T s) { return mk<T>(a.x * s, a.y * s); }
+template <typename T> __device__ __forceinline__ C<T> scale(C<T> a, T s) {
+  if constexpr (sizeof(T) == 4) return pmul_s(a, s);
+  else return mk<T>(a.x * s, a.y * s);
+}
 // multiply by (s*i), s = +-1
 template <typename T, int S> __device__ __forceinline__ C<T> mul_si(C<T> a) {
   return S > 0 ? mk<T>(-a.y, a.x) : mk<T>(a.y, -a.x);
@@ -33,9 +70,22 @@ template <> struct consts<double> { static constexpr double rsqrt2 = 0.707106781
 template <typename T, int S> __device__ __forceinline__ void dft2(C<T>& a, C<T>& b) {
   C<T> t = sub<T>(a, b); a = add<T>(a, b); b = t;
 }
+// a +- (S i) d, componentwise (scalar: the swap would cost more than it saves)
+template <typename T, int S> __device__ __forceinline__ C<T> add_si(C<T> a, C<T> d) {
+  return mk<T>(a.x - S * d.y, a.y + S * d.x);
+}
+template <typename T, int S> __device__ __forceinline__ C<T> sub_si(C<T> a, C<T> d) {
+  return mk<T>(a.x + S * d.y, a.y - S * d.x);
+}
 template <typename T, int S> __device__ __forceinline__ void dft4(C<T>& v0, C<T>& v1, C<T>& v2, C<T>& v3) {
-  C<T> a0 = add<T>(v0, v2), a1 = sub<T>(v0, v2), a2 = add<T>(v1, v3), a3 = mul_si<T, S>(sub<T>(v1, v3));
-  v0 = add<T>(a0, a2); v2 = sub<T>(a0, a2); v1 = add<T>(a1, a3); v3 = sub<T>(a1, a3);
+  if constexpr (sizeof(T) == 4) {
+    const float2 a0 = padd(v0, v2), a1 = psub(v0, v2), a2 = padd(v1, v3), d = psub(v1, v3);
+    v0 = padd(a0, a2); v2 = psub(a0, a2);
+    v1 = add_si<T, S>(a1, d); v3 = sub_si<T, S>(a1, d);
+  } else {
+    C<T> a0 = add<T>(v0, v2), a1 = sub<T>(v0, v2), a2 = add<T>(v1, v3), a3 = mul_si<T, S>(sub<T>(v1, v3));
+    v0 = add<T>(a0, a2); v2 = sub<T>(a0, a2); v1 = add<T>(a1, a3); v3 = sub<T>(a1, a3);
+  }
 }
 // v[0..7] -> X[q] in v[q]
 template <typename T, int S> __device__ __forceinline__ void dft8(C<T>* v) {
@@ -44,6 +94,16 @@ template <typename T, int S> __device__ __forceinline__ void dft8(C<T>* v) {
   dft4<T, S>(e0, e1, e2, e3);
   dft4<T, S>(o0, o1, o2, o3);
   const T r = consts<T>::rsqrt2;
+  if constexpr (sizeof(T) == 4) {
+    // w8 o1 = r (o1.x - S o1.y, o1.y + S o1.x); w8^3 o3 = -r (o3.x + S o3.y, o3.y - S o3.x)
+    const float2 u1 = mk<T>(o1.x - S * o1.y, o1.y + S * o1.x);
+    const float2 u3 = mk<T>(o3.x + S * o3.y, o3.y - S * o3.x);
+    v[0] = padd(e0, o0); v[4] = psub(e0, o0);
+    v[1] = pfma_s(u1, r, e1); v[5] = pfma_s(u1, -r, e1);
+    v[2] = add_si<T, S>(e2, o2); v[6] = sub_si<T, S>(e2, o2);
+    v[3] = pfma_s(u3, -r, e3); v[7] = pfma_s(u3, r, e3);
+    return;
+  }
   // w8 = exp(S*2*pi*i/8) = (1 + S i)/sqrt2 ; w8^2 = S i ; w8^3 = (-1 + S i)/sqrt2
   C<T> t1 = mk<T>(r * (o1.x - S * o1.y), r * (o1.y + S * o1.x));
   C<T> t2 = mul_si<T, S>(o2);
@@ -105,6 +165,22 @@ __host__ __device__ __forceinline__ int dig_pos(int k, int logL, int r0) {
 __host__ __device__ __forceinline__ int tw_off8(int logL, int r0, int ls) {
   const int top = 1 << (logL - r0);
   return (r0 ? top : 0) + (top - (8 << ls)) / 7;
+}
+
+// v[q] *= w^q, q = 1..7, with the same products as powers8 but each power
+// formed just before it is used (fewer values live at once).
+template <typename T>
+__device__ __forceinline__ void twiddle8(C<T>* v, C<T> w) {
+  const C<T> w2 = mul<T>(w, w);
+  v[1] = mul<T>(v[1], w);
+  v[2] = mul<T>(v[2], w2);
+  const C<T> w3 = mul<T>(w2, w);
+  v[3] = mul<T>(v[3], w3);
+  const C<T> w4 = mul<T>(w2, w2);
+  v[4] = mul<T>(v[4], w4);
+  v[5] = mul<T>(v[5], mul<T>(w4, w));
+  v[6] = mul<T>(v[6], mul<T>(w3, w3));
+  v[7] = mul<T>(v[7], mul<T>(w4, w3));
 }
 
 template <typename T>

@@ -79,10 +79,7 @@ struct FftC {
   static __device__ __forceinline__ void stage0_fwd(C<T>* v, int t, const C<T>* tw) {
     if (R0 == 0) {
       dft8<T, -1>(v);
-      C<T> wp[8];
-      powers8<T>(__ldg(tw + t), wp);
-#pragma unroll
-      for (int q = 1; q < 8; ++q) v[q] = mul<T>(v[q], wp[q]);
+      twiddle8<T>(v, __ldg(tw + t));
     } else if (R0 == 2) {
 #pragma unroll
       for (int i = 0; i < 2; ++i) {
@@ -103,10 +100,7 @@ struct FftC {
   // inverse of stage 0 (DIT: conjugate twiddle, then butterfly)
   static __device__ __forceinline__ void stage0_inv(C<T>* v, int t, const C<T>* tw) {
     if (R0 == 0) {
-      C<T> wp[8];
-      powers8<T>(conj<T>(__ldg(tw + t)), wp);
-#pragma unroll
-      for (int r = 1; r < 8; ++r) v[r] = mul<T>(v[r], wp[r]);
+      twiddle8<T>(v, conj<T>(__ldg(tw + t)));
       dft8<T, 1>(v);
     } else if (R0 == 2) {
 #pragma unroll
@@ -136,12 +130,7 @@ struct FftC {
 #pragma unroll
     for (int r = 0; r < 8; ++r) v[r] = buf[sb ^ sw(r << ls)];
     dft8<T, -1>(v);
-    if (ls > 0) {
-      C<T> wp[8];
-      powers8<T>(__ldg(tw + tw_off8(LOGL, R0, ls) + o), wp);
-#pragma unroll
-      for (int q = 1; q < 8; ++q) v[q] = mul<T>(v[q], wp[q]);
-    }
+    if (ls > 0) twiddle8<T>(v, __ldg(tw + tw_off8(LOGL, R0, ls) + o));
 #pragma unroll
     for (int q = 0; q < 8; ++q) buf[sb ^ sw(q << ls)] = v[q];
   }
@@ -151,12 +140,7 @@ struct FftC {
     C<T> v[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) v[r] = buf[sb ^ sw(r << ls)];
-    if (ls > 0) {
-      C<T> wp[8];
-      powers8<T>(conj<T>(__ldg(tw + tw_off8(LOGL, R0, ls) + o)), wp);
-#pragma unroll
-      for (int r = 1; r < 8; ++r) v[r] = mul<T>(v[r], wp[r]);
-    }
+    if (ls > 0) twiddle8<T>(v, conj<T>(__ldg(tw + tw_off8(LOGL, R0, ls) + o)));
     dft8<T, 1>(v);
 #pragma unroll
     for (int q = 0; q < 8; ++q) buf[sb ^ sw(q << ls)] = v[q];
@@ -251,6 +235,89 @@ __device__ __forceinline__ T pro_apply(const PassArgs<T>& a, size_t i, const PIn
     const T tv = x.s ? x.g + beta * x.t : (T)0;
     a.f.t[i] = tv;
     return tv;
+  }
+}
+
+// Split the packed length-M transforms of the rows row0 .. row0+nb-1 (shared
+// memory, digit-reversed) into the half spectra X[0..M] and store them
+// transposed, W[k][row0 + bb].  With z the packed transform,
+//   X[k] = (z[k] + conj z[M-k]) / 2 + w_k (z[k] - conj z[M-k]) / (2i),
+// w_k = exp(-i pi k / M), and w_{M-k} = -conj w_k, so one work item computes
+// X[k] and X[M-k] from the same two values.  FP32 with an even row count and
+// even W rows: each item takes two rows and stores 16 bytes per k.
+template <typename T>
+__device__ __forceinline__ void split_two(const C<T>* s, int pk, int pm, C<T> w, C<T>& xk, C<T>& xm) {
+  const C<T> a = s[pk], b = s[pm];
+  {
+    const C<T> zm = conj<T>(b);
+    const C<T> E = scale<T>(add<T>(a, zm), (T)0.5);
+    const C<T> dl = sub<T>(a, zm);
+    xk = add<T>(E, mul<T>(w, mk<T>((T)0.5 * dl.y, (T)-0.5 * dl.x)));
+  }
+  {
+    const C<T> zm = conj<T>(a);
+    const C<T> E = scale<T>(add<T>(b, zm), (T)0.5);
+    const C<T> dl = sub<T>(b, zm);
+    xm = add<T>(E, mul<T>(mk<T>(-w.x, w.y), mk<T>((T)0.5 * dl.y, (T)-0.5 * dl.x)));
+  }
+}
+template <typename T, int M>
+__device__ __forceinline__ void split_store(const C<T>* sm, int rs, int nb, int lognb, int row0, int nrows,
+                                            const int* sp, const C<T>* tws, C<T>* W, int rows_w) {
+  constexpr int hm = M / 2 + 1;
+  const int rows = min(nb, nrows - row0);
+  if (sizeof(T) == 4 && nb >= 2 && (rows_w & 1) == 0) {
+    const int lp = lognb - 1;  // row pairs per group
+    for (int idx = threadIdx.x; idx < hm << lp; idx += blockDim.x) {
+      const int k = idx >> lp, b0 = 2 * (idx & ((1 << lp) - 1));
+      if (b0 >= rows) continue;
+      const bool two = b0 + 1 < rows;
+      const C<T>* s0 = sm + b0 * rs;
+      const C<T>* s1 = s0 + rs;
+      C<T> xk0, xm0, xk1 = mk<T>(0, 0), xm1 = mk<T>(0, 0);
+      if (k == 0) {
+        const C<T> z0 = s0[0];
+        xk0 = mk<T>(z0.x + z0.y, (T)0);
+        xm0 = mk<T>(z0.x - z0.y, (T)0);
+        if (two) {
+          const C<T> z1 = s1[0];
+          xk1 = mk<T>(z1.x + z1.y, (T)0);
+          xm1 = mk<T>(z1.x - z1.y, (T)0);
+        }
+      } else {
+        const int pk = __ldg(sp + k), pm = __ldg(sp + M - k);
+        const C<T> w = __ldg(tws + k);
+        split_two<T>(s0, pk, pm, w, xk0, xm0);
+        if (two) split_two<T>(s1, pk, pm, w, xk1, xm1);
+      }
+      const int km = k == 0 ? M : M - k;
+      C<T>* wk = W + (size_t)k * rows_w + row0 + b0;
+      C<T>* wm = W + (size_t)km * rows_w + row0 + b0;
+      if (two) {
+        *reinterpret_cast<float4*>(wk) = make_float4((float)xk0.x, (float)xk0.y, (float)xk1.x, (float)xk1.y);
+        if (km != k) *reinterpret_cast<float4*>(wm) = make_float4((float)xm0.x, (float)xm0.y, (float)xm1.x, (float)xm1.y);
+      } else {
+        wk[0] = xk0;
+        if (km != k) wm[0] = xm0;
+      }
+    }
+    return;
+  }
+  for (int idx = threadIdx.x; idx < hm << lognb; idx += blockDim.x) {
+    const int k = idx >> lognb, bb = idx & (nb - 1);
+    if (bb >= rows) continue;
+    const C<T>* s = sm + bb * rs;
+    C<T> xk, xm;
+    if (k == 0) {
+      const C<T> z0 = s[0];
+      xk = mk<T>(z0.x + z0.y, (T)0);
+      xm = mk<T>(z0.x - z0.y, (T)0);
+    } else {
+      split_two<T>(s, __ldg(sp + k), __ldg(sp + M - k), __ldg(tws + k), xk, xm);
+    }
+    const int km = k == 0 ? M : M - k;
+    W[(size_t)k * rows_w + row0 + bb] = xk;
+    if (km != k) W[(size_t)km * rows_w + row0 + bb] = xm;
   }
 }
 
@@ -353,29 +420,8 @@ __global__ void BEM_ROW_BOUNDS(LOGL) k_pass_a(PassArgs<T> a) {
     }
   }
   // split the packed transform into the half spectrum, store transposed
-  const Cx* tws = reinterpret_cast<const Cx*>(a.twS);
-  const int* sp = a.spA;
-  Cx* W = reinterpret_cast<Cx*>(a.W);
-#pragma unroll 3
-  for (int idx = tid; idx < (M + 1) << lognb; idx += nthr) {
-    const int k = idx >> lognb, bb = idx & (nb - 1);
-    const int rw = row0 + bb;
-    if (rw >= nrows) continue;
-    const Cx* s = sm + bb * rs;
-    Cx X;
-    if (k == 0 || k == M) {
-      const Cx z0 = s[0];
-      X = mk<T>(k == 0 ? z0.x + z0.y : z0.x - z0.y, (T)0);
-    } else {
-      const Cx zk = s[__ldg(sp + k)];
-      const Cx zm = conj<T>(s[__ldg(sp + M - k)]);
-      const Cx E = scale<T>(add<T>(zk, zm), (T)0.5);
-      const Cx dlt = sub<T>(zk, zm);
-      const Cx O = mk<T>((T)0.5 * dlt.y, (T)-0.5 * dlt.x);  // (zk - zm) / (2i)
-      X = add<T>(E, mul<T>(__ldg(tws + k), O));
-    }
-    W[(size_t)k * a.rows_w + rw] = X;
-  }
+  split_store<T, M>(sm, rs, nb, lognb, row0, nrows, a.spA, reinterpret_cast<const Cx*>(a.twS),
+                    reinterpret_cast<Cx*>(a.W), a.rows_w);
 }
 
 // ---------------------------------------------------------------------------
@@ -538,26 +584,7 @@ __global__ void BEM_ROWP_BOUNDS(LOGL) k_pass_ap(PassArgs<T> a) {
       F::dif(buf, t, ls, tw);
       __syncthreads();
     }
-#pragma unroll 3
-    for (int idx = tid; idx < (M + 1) << lognb; idx += nthr) {
-      const int k = idx >> lognb, bb = idx & (nb - 1);
-      const int rw = row0 + bb;
-      if (rw >= nrows) continue;
-      const Cx* s = sm + bb * rs;
-      Cx X;
-      if (k == 0 || k == M) {
-        const Cx z0 = s[0];
-        X = mk<T>(k == 0 ? z0.x + z0.y : z0.x - z0.y, (T)0);
-      } else {
-        const Cx zk = s[__ldg(sp + k)];
-        const Cx zm = conj<T>(s[__ldg(sp + M - k)]);
-        const Cx E = scale<T>(add<T>(zk, zm), (T)0.5);
-        const Cx dlt = sub<T>(zk, zm);
-        const Cx O = mk<T>((T)0.5 * dlt.y, (T)-0.5 * dlt.x);
-        X = add<T>(E, mul<T>(__ldg(tws + k), O));
-      }
-      W[(size_t)k * a.rows_w + rw] = X;
-    }
+    split_store<T, M>(sm, rs, nb, lognb, row0, nrows, sp, tws, W, a.rows_w);
   }
   if (MODE == A_PK_P) {
     double vv[3] = {(double)acc[0], (double)acc[1], (double)acc[2]};
@@ -572,7 +599,7 @@ __global__ void BEM_ROWP_BOUNDS(LOGL) k_pass_ap(PassArgs<T> a) {
 // ---------------------------------------------------------------------------
 // Pass B: nbB columns per CTA, Py/8 threads per column; columns kx = 0..M.
 #ifndef BEM_COL_MIN_BLOCKS
-#define BEM_COL_MIN_BLOCKS 3
+#define BEM_COL_MIN_BLOCKS 2
 #endif
 template <typename T, int MODE, int LOGL>
 __global__ void __launch_bounds__((LOGL) >= 13 ? 1024 : 512, (LOGL) >= 13 ? 1 : BEM_COL_MIN_BLOCKS)
