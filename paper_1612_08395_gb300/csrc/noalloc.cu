@@ -127,7 +127,10 @@ extern "C" int bem_convolve_noalloc(const double* khat, int Nx, int Ny, double c
   pl.nbB = nbb; pl.gB = bem::make_geo(ilog2i(py), nbb, 8);
   pl.threadsB = nbb * tb; pl.gridB = (M + 1 + nbb - 1) / nbb;
   pl.smemB = (size_t)nbb * pl.gB.rs * 16;
-  pl.nsm = 1;  // only the plain passes run here, never the persistent ones
+  int nsm = 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+    return bem::set_error(BEM_ECUDA, "bem_convolve_noalloc: cannot query the SM count");
+  pl.nsm = nsm;  // the persistent row passes size their grids by it
   // every pass stays within the default 48 KB of dynamic shared memory here
   if (pl.smemA > 48 * 1024 || pl.smemB > 48 * 1024 || pl.smemC > 48 * 1024)
     return bem::set_error(BEM_EINVAL, "bem_convolve_noalloc: grid too large for the default shared memory");
