@@ -12,7 +12,13 @@ value       : CG iterations of all ranks / max-over-ranks device time (CUDA even
 e2e         : the same through the C ABI with pinned host buffers (profile in,
               pressure out), wall clock around the call
 roofline    : the dominant transform pass, algorithmic bytes / its live average
-              duration (CUDA events recorded inside the captured CG graphs)
+              duration (CUDA events recorded inside the captured CG graphs); the
+              library counts each timed launch's bytes and flops from the torus
+              and rows that launch worked on (bem_pass_work)
+roofline_full_torus : the same for the passes of the non-adhesive preload solve
+              repeated after the timed region: every launch transforms the
+              whole 4096^2 torus (the fixed-set iterations of the sweep run on
+              the contact box's smaller torus)
 cpu_baseline: the FP64 oracle (numpy FFT mode) on a bounded sample of the same
               workload, on this host's cores
 
@@ -29,7 +35,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -120,44 +125,9 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def pass_flops(nx, ny, px, py):
-    """Algorithmic FP32 flops of one launch of each transform pass (5 L log2 L per
-    complex FFT of length L, halved for a transform with half its inputs zero
-    or half its outputs dropped), plus the split/spectrum work."""
-    M = px // 2
-    lm, lp = math.log2(M), math.log2(py)
-    fft_m = 5 * M * lm
-    fft_p = 5 * py * lp
-    a = ny * (0.5 * fft_m + 20 * M)            # row FFT, half the inputs zero, split
-    b = (M + 1) * (2 * 0.5 * fft_p + 8 * py)    # column FFT and its inverse, pruned, multiply
-    c = ny * (0.5 * fft_m + 20 * M)            # packing, row inverse keeping half
-    return {"A": a, "B": b, "C": c}
-
-
 def fp32_peak_tflops(sm_mhz):
     """FP32 vector peak: 152 SMs x 128 lanes x 2 flops (FMA) x clock."""
     return 152 * 128 * 2 * (sm_mhz or 2070.0) * 1e6 / 1e12
-
-
-def pass_bytes(nx, ny, px, py, mode):
-    """Algorithmic HBM bytes of one launch of each transform pass, FP32 fields.
-
-    W (the transposed half spectrum) holds (Px/2+1) x Ny complex64; the
-    spectrum quarter (Px/2+1) x (Py/2+1) float32.  mode 'pk': pass A reads
-    p, t, g and writes p (Polonsky-Keer update); pass C reads c, p and writes
-    g.  mode 'cg': pass A reads S, g, t, writes t; pass C reads S, t, writes r.
-    """
-    n = nx * ny
-    w = 8 * (px // 2 + 1) * ny
-    khat = 4 * (px // 2 + 1) * (py // 2 + 1)
-    if mode == "pk":
-        a = 16 * n + w
-        c = w + 12 * n
-    else:
-        a = 13 * n + w
-        c = w + 9 * n
-    b = 2 * w + khat
-    return {"A": a, "B": b, "C": c}
 
 
 def aggregate(elapsed_s, iters, world, device):
@@ -389,6 +359,7 @@ def main():
     torch.cuda.synchronize()
     clocks = sampler.stop()
     launches = h.info().kernel_launches - launches0
+    work_bytes, work_flops = h.pass_work()
     pass_ms, pass_n, pass_cg = h.pass_times(reset=True)
     elapsed = sum(step_ms) / 1e3
     elapsed_max, iters_all = aggregate(elapsed, iters_total, world, "cuda")
@@ -413,11 +384,25 @@ def main():
     dom = int(np.argmax(avg_ms))
     names = ["A", "B", "C"]
     frac_cg = pass_cg / max(pass_n, 1)
-    bpk = pass_bytes(N, N, info.Px, info.Py, "pk")
-    bcg = pass_bytes(N, N, info.Px, info.Py, "cg")
-    bytes_dom = (1 - frac_cg) * bpk[names[dom]] + frac_cg * bcg[names[dom]]
-    flops_dom = pass_flops(N, N, info.Px, info.Py)[names[dom]]
+    bytes_dom = work_bytes[dom]
+    flops_dom = work_flops[dom]
     achieved = bytes_dom / (avg_ms[dom] * 1e-3) / 1e9
+
+    # the full 2048^2 torus: passes of the Polonsky-Keer preload solve (every
+    # iteration transforms all rows), timed the same way, outside the timed region
+    h.pass_times(reset=True)
+    for _ in range(3):
+        h.solve(prof_d, D0, precision=args.precision, stream=stream, time_passes=True)
+    torch.cuda.synchronize()
+    fb, _ = h.pass_work()
+    fms, fn, _ = h.pass_times(reset=True)
+    favg = [m / max(fn, 1) for m in fms]
+    fdom = int(np.argmax(favg))
+    full = {"kernel": f"pass {names[fdom]}", "bound": "hbm",
+            "achieved": fb[fdom] / (favg[fdom] * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+            "frac": fb[fdom] / (favg[fdom] * 1e-3) / 1e9 / hbm,
+            "avg_ms": {k: v for k, v in zip(names, favg)}, "bytes_per_launch": fb[fdom],
+            "timed_launches": fn, "workload": "non-adhesive preload solve, 2048^2 grid, 4096^2 torus"}
 
     forces = [r.force for r in results]
     counts = [r.contact_count for r in results]
@@ -442,11 +427,13 @@ def main():
                      "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
                      "avg_ms": {k: v for k, v in zip(names, avg_ms)}, "timed_launches": pass_n,
                      "bytes_per_launch": bytes_dom,
+                     "fixed_set_fraction": frac_cg,
                      "alu": {"achieved": flops_dom / (avg_ms[dom] * 1e-3) / 1e12,
                              "peak": fp32_peak_tflops(clocks.get("sm_max_mhz")), "unit": "TFLOP/s",
                              "frac": flops_dom / (avg_ms[dom] * 1e-3) / 1e12
                              / fp32_peak_tflops(clocks.get("sm_max_mhz")),
                              "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}},
+        "roofline_full_torus": full,
         "clocks": clocks,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 8 * N * N + 8 * len(ds),
                 "d2h_bytes_per_step": 8 * N * N + 56 * len(ds)},

@@ -215,6 +215,18 @@ int bem_set_material(bem_handle h, double nu, double E0, double c0);
  * the passes run on. */
 int bem_pass_times(bem_handle h, double ms[3], long long count[2], int reset);
 
+/* Average algorithmic work of one timed launch of each pass (A, B, C), over
+ * the launches counted by bem_pass_times (read it before a reset): bytes[i] =
+ * the fields the pass's mode reads and writes, the intermediate W and (pass B)
+ * the spectrum quarter; flops[i] = 5 L log2 L per complex FFT of length L,
+ * halved where half the inputs are zero or half the outputs are dropped.  The
+ * counts follow the torus and rows each launch worked on: in the fixed-set CG
+ * of the adhesive algorithm (Sec. 3.1) the passes touch only the rows between
+ * the first and last row of the contact set, and a solve whose contact set
+ * fits a box of at most half the torus runs on a smaller torus (the operator
+ * restricted to the set couples only elements of the set). */
+int bem_pass_work(bem_handle h, double bytes[3], double flops[3]);
+
 /* ---------------------------------------------------------------------------
  * bem_convolve_noalloc: u = A K*p in FP64 for callers that must not allocate
  * device memory.  The paper has no counterpart; this is a service of the

@@ -103,6 +103,7 @@ def load_library(path: str = LIB_PATH):
     lib.bem_get_info.argtypes = [vp, ctypes.POINTER(Info)]
     lib.bem_convolve_noalloc.argtypes = [vp, ip, ip, ctypes.c_double, vp, vp, vp]
     lib.bem_pass_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong), ip]
+    lib.bem_pass_work.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     for fn in (lib.bem_alpha, lib.bem_c1_corrected):
         fn.restype = ctypes.c_double
     lib.bem_alpha.argtypes = [ctypes.c_double, ctypes.c_double]
@@ -220,6 +221,14 @@ class Handle:
         cnt = (ctypes.c_longlong * 2)()
         _check(load_library().bem_pass_times(self._h, ms, cnt, 1 if reset else 0))
         return list(ms), cnt[0], cnt[1]
+
+    def pass_work(self):
+        """(bytes[A, B, C], flops[A, B, C]): average algorithmic work per timed launch
+        (read before a pass_times reset)."""
+        b = (ctypes.c_double * 3)()
+        f = (ctypes.c_double * 3)()
+        _check(load_library().bem_pass_work(self._h, b, f))
+        return list(b), list(f)
 
     def influence_table(self) -> np.ndarray:
         inf = self.info()

@@ -48,6 +48,10 @@ struct Scalars {
   double sum_p, sum_dp, n_ol, n_ic, str, eps_min;
   int max_iter, iter, done, status, have_tau, it_min;
   int nA, pad1;   // CTAs of the last pass A launch (its partials feed pass C)
+  // Rows band0 .. band1 and columns col0 .. col1 hold every element of the
+  // fixed contact set S (band0 > band1: S is empty); written by k_box at the
+  // start of a fixed-set solve.
+  int band0, band1, col0, col1;
   unsigned int cnt_a, cnt_c, cnt_e, cnt_r;  // last-block arrival counters
   // Sticky device error bits (kept across solves: init_scalars does not copy
   // this member); 1 = a kernel gave up waiting for its own asynchronous copies.
@@ -111,6 +115,7 @@ struct PassArgs {
   double* partC;
   Scalars* sc;
   unsigned int* kerr;   // sticky error word (may be null: errors then go unreported)
+  int use_band;         // fixed-set CG loop: restrict the passes to rows sc->band0 .. band1
 };
 
 template <typename T> void launch_pass_a(const PassArgs<T>& a, int mode, cudaStream_t s);
@@ -122,6 +127,13 @@ template <typename T> void launch_pk_init(const Plan& pl, const double* h64, dou
                                           T* t, int warm, int ngrid, cudaStream_t s);
 template <typename T> void launch_cg_update(const Plan& pl, Fields<T> f, double* part, Scalars* sc,
                                             int ngrid, cudaStream_t s);
+void launch_box(const Plan& pl, const uint8_t* S, Scalars* sc, cudaStream_t s);
+// Copy the box [x0, x0+bx) x [y0, y0+by) of the nx x ny fields p, c, S into
+// bx x by sub-grid fields (zero where the box leaves the grid), and back for p.
+template <typename T> void launch_box_gather(const T* p, const T* c, const uint8_t* S, int nx, int ny, int x0,
+                                             int y0, T* bp, T* bc, uint8_t* bS, int bx, int by, cudaStream_t s);
+template <typename T> void launch_box_scatter(const T* bp, T* p, int nx, int ny, int x0, int y0, int bx, int by,
+                                              cudaStream_t s);
 template <typename T> void launch_detach(const Plan& pl, Fields<T> f, double* part, Scalars* sc,
                                          int ngrid, cudaStream_t s);
 template <typename T> void launch_stats(const Plan& pl, const T* p, const T* g, const uint8_t* S,

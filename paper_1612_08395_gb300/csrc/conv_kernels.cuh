@@ -534,9 +534,16 @@ __global__ void BEM_ROWP_BOUNDS(LOGL) k_pass_ap(PassArgs<T> a) {
   if (tid == 0) mbar_init(&bar, 1);
   __syncthreads();
   unsigned phase = 0;
-  int g = blockIdx.x;
-  if (g < G) pro_prefetch<T, MODE>(a, st, ss, g * nb, min(nb, nrows - g * nb), ncols, nb, &bar);
-  for (; g < G; g += gridDim.x) {
+  // row groups g0 .. gend-1 (fixed-set CG: the contact band only; the rows of W
+  // outside it are not written and pass B treats them as zero)
+  int g0 = 0, gend = G;
+  if (MODE == A_CG_T && a.use_band) {
+    g0 = sc->band0 / nb;
+    gend = sc->band1 >= sc->band0 ? sc->band1 / nb + 1 : g0;
+  }
+  int g = g0 + blockIdx.x;
+  if (g < gend) pro_prefetch<T, MODE>(a, st, ss, g * nb, min(nb, nrows - g * nb), ncols, nb, &bar);
+  for (; g < gend; g += gridDim.x) {
     const int row0 = g * nb, row = row0 + b;
     const bool act = row < nrows;
     const size_t rowoff = (size_t)row * ncols;
@@ -556,7 +563,7 @@ __global__ void BEM_ROWP_BOUNDS(LOGL) k_pass_ap(PassArgs<T> a) {
     }
     __syncthreads();  // staging consumed: refill it for the next group
     const int gn = g + gridDim.x;
-    if (gn < G) pro_prefetch<T, MODE>(a, st, ss, gn * nb, min(nb, nrows - gn * nb), ncols, nb, &bar);
+    if (gn < gend) pro_prefetch<T, MODE>(a, st, ss, gn * nb, min(nb, nrows - gn * nb), ncols, nb, &bar);
     Cx v[8];
     T* out = pro_out<T, MODE>(a);
 #pragma unroll
@@ -623,6 +630,12 @@ __global__ void __launch_bounds__((LOGL) >= 13 ? 1024 : 512, (LOGL) >= 13 ? 1 : 
   const int* sp = a.spB;
   Cx* W = reinterpret_cast<Cx*>(a.W);
   const size_t coff = (size_t)(act ? kx : 0) * rin;
+  // rows of W that can be nonzero: all, or the contact band in the fixed-set CG loop
+  int ylo = 0, yhi = rin - 1;
+  if (MODE == B_CONV && a.use_band) {
+    ylo = a.sc->band0;
+    yhi = min(a.sc->band1, rin - 1);
+  }
 
   Cx v[8];
 #pragma unroll
@@ -630,7 +643,7 @@ __global__ void __launch_bounds__((LOGL) >= 13 ? 1024 : 512, (LOGL) >= 13 ? 1 : 
     v[e] = mk<T>(0, 0);
     if (HALF && !F::first_half(e)) continue;
     const int y = F::n0(t, e);
-    if (act && y < rin) v[e] = W[coff + y];
+    if (act && y >= ylo && y <= yhi) v[e] = W[coff + y];
   }
   F::stage0_fwd(v, t, tw);
 #pragma unroll
@@ -688,7 +701,7 @@ __global__ void __launch_bounds__((LOGL) >= 13 ? 1024 : 512, (LOGL) >= 13 ? 1 : 
     for (int e = 0; e < 8; ++e) {
       if (!F::first_half(e)) continue;
       const int y = F::n0(t, e);
-      if (y < rin) W[coff + y] = v[e];
+      if (y >= ylo && y <= yhi) W[coff + y] = v[e];
     }
   }
   (void)R0;
@@ -1127,12 +1140,18 @@ __global__ void BEM_ROWP_BOUNDS(LOGL) k_pass_cp(PassArgs<T> a) {
   const T us = (T)a.uscale;
   T acc[3] = {0, 0, 0};
   const int half = (nx + 1) >> 1;
-  int g = blockIdx.x;
-  if (g < G) {
+  // row groups g0 .. gend-1 (fixed-set CG: the contact band only; r = 0 outside it)
+  int g0 = 0, gend = G;
+  if (MODE == C_CG_R && a.use_band) {
+    g0 = sc->band0 / nb;
+    gend = sc->band1 >= sc->band0 ? sc->band1 / nb + 1 : g0;
+  }
+  int g = g0 + blockIdx.x;
+  if (g < gend) {
     prefetch_w(g);
     if (EpiStage<MODE>::any) prefetch_e(g);
   }
-  for (; g < G; g += gridDim.x) {
+  for (; g < gend; g += gridDim.x) {
     const int row0 = g * nb;
     cp_async_wait_all();  // W of this group
     __syncthreads();
@@ -1157,7 +1176,7 @@ __global__ void BEM_ROWP_BOUNDS(LOGL) k_pass_cp(PassArgs<T> a) {
     }
     __syncthreads();  // W staging consumed
     const int gn = g + gridDim.x;
-    if (gn < G) prefetch_w(gn);
+    if (gn < gend) prefetch_w(gn);
 #pragma unroll
     for (int ls = 0; ls <= F::LS_TOP; ls += 3) {
       F::dit(buf, t, ls, tw);
@@ -1209,7 +1228,7 @@ __global__ void BEM_ROWP_BOUNDS(LOGL) k_pass_cp(PassArgs<T> a) {
       }
     }
     __syncthreads();  // epilogue staging and transform rows consumed
-    if (gn < G && EpiStage<MODE>::any) prefetch_e(gn);
+    if (gn < gend && EpiStage<MODE>::any) prefetch_e(gn);
   }
   cp_async_wait_all();
   if (MODE == C_PLAIN || MODE == C_GAP) return;
@@ -1242,6 +1261,30 @@ __global__ void k_pk_init(int n, const double* __restrict__ h64, double d, T* __
   }
 }
 
+// Contact-box sub-grid: gather p, c, S of the box (zero outside the grid), and
+// scatter p back (in-grid elements only).  bx is a power of two.
+template <typename T>
+__global__ void k_box_gather(const T* __restrict__ p, const T* __restrict__ c, const uint8_t* __restrict__ S,
+                             int nx, int ny, int x0, int y0, T* __restrict__ bp, T* __restrict__ bc,
+                             uint8_t* __restrict__ bS, int lbx, int nb) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x) {
+    const int X = x0 + (i & ((1 << lbx) - 1)), Y = y0 + (i >> lbx);
+    const bool in = X < nx && Y < ny;
+    const size_t src = in ? (size_t)Y * nx + X : 0;
+    bp[i] = in ? p[src] : (T)0;
+    bc[i] = in ? c[src] : (T)0;
+    bS[i] = in ? S[src] : (uint8_t)0;
+  }
+}
+template <typename T>
+__global__ void k_box_scatter(const T* __restrict__ bp, T* __restrict__ p, int nx, int ny, int x0, int y0,
+                              int lbx, int nb) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x) {
+    const int X = x0 + (i & ((1 << lbx) - 1)), Y = y0 + (i >> lbx);
+    if (X < nx && Y < ny) p[(size_t)Y * nx + X] = bp[i];
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ T cg_update_one(T* __restrict__ p, T* __restrict__ g, const T* __restrict__ t,
                                            const T* __restrict__ r, int i, T tau) {
@@ -1255,17 +1298,20 @@ __device__ __forceinline__ T cg_update_one(T* __restrict__ p, T* __restrict__ g,
 // the new G, beta and the convergence test.  Four elements per thread and
 // trip through vector loads when the pointers allow it.
 template <typename T>
-__global__ void k_cg_update(int n, Fields<T> f, double* part, Scalars* sc) {
+__global__ void k_cg_update(int nx, Fields<T> f, double* part, Scalars* sc) {
   __shared__ double red[3 * 32];
   __shared__ int lastflag;
   if (sc->done) return;
   const T tau = (T)sc->tau;
   T acc = 0;
-  T* __restrict__ p = f.p;
-  T* __restrict__ g = f.g;
-  const T* __restrict__ t = f.t;
-  const T* __restrict__ r = f.r;
-  if (sizeof(T) == 4 && (n & 3) == 0) {
+  // only the rows of the contact band: t and r vanish outside it
+  const size_t off = (size_t)sc->band0 * nx;
+  const int n = sc->band1 >= sc->band0 ? (sc->band1 - sc->band0 + 1) * nx : 0;
+  T* __restrict__ p = f.p + off;
+  T* __restrict__ g = f.g + off;
+  const T* __restrict__ t = f.t + off;
+  const T* __restrict__ r = f.r + off;
+  if (sizeof(T) == 4 && (nx & 3) == 0) {
     using V = float4;
     V* pv = reinterpret_cast<V*>(p);
     V* gv = reinterpret_cast<V*>(g);
@@ -1614,9 +1660,24 @@ void launch_pk_init(const Plan& pl, const double* h64, double d, T* c, T* p, T* 
   k_pk_init<T><<<ngrid, 256, 0, s>>>(pl.nx * pl.ny, h64, d, c, p, t, warm);
 }
 template <typename T>
+void launch_box_gather(const T* p, const T* c, const uint8_t* S, int nx, int ny, int x0, int y0, T* bp, T* bc,
+                       uint8_t* bS, int bx, int by, cudaStream_t s) {
+  int lbx = 0;
+  while ((1 << lbx) < bx) ++lbx;
+  const int nb = bx * by;
+  k_box_gather<T><<<ew_grid((size_t)nb), 256, 0, s>>>(p, c, S, nx, ny, x0, y0, bp, bc, bS, lbx, nb);
+}
+template <typename T>
+void launch_box_scatter(const T* bp, T* p, int nx, int ny, int x0, int y0, int bx, int by, cudaStream_t s) {
+  int lbx = 0;
+  while ((1 << lbx) < bx) ++lbx;
+  const int nb = bx * by;
+  k_box_scatter<T><<<ew_grid((size_t)nb), 256, 0, s>>>(bp, p, nx, ny, x0, y0, lbx, nb);
+}
+template <typename T>
 void launch_cg_update(const Plan& pl, Fields<T> f, double* part, Scalars* sc, int ngrid,
                       cudaStream_t s) {
-  k_cg_update<T><<<ngrid, 256, 0, s>>>(pl.nx * pl.ny, f, part, sc);
+  k_cg_update<T><<<ngrid, 256, 0, s>>>(pl.nx, f, part, sc);
 }
 template <typename T>
 void launch_detach(const Plan& pl, Fields<T> f, double* part, Scalars* sc, int ngrid,
@@ -1663,6 +1724,9 @@ void launch_mask_field(T* x, const uint8_t* S, size_t n, cudaStream_t s) {
 #define BEM_INSTANTIATE_EW(T)                                                                  \
   template void launch_pk_init<T>(const Plan&, const double*, double, T*, T*, T*, int, int,    \
                                   cudaStream_t);                                               \
+  template void launch_box_gather<T>(const T*, const T*, const uint8_t*, int, int, int, int, T*, T*, \
+                                     uint8_t*, int, int, cudaStream_t);                         \
+  template void launch_box_scatter<T>(const T*, T*, int, int, int, int, int, int, cudaStream_t); \
   template void launch_cg_update<T>(const Plan&, Fields<T>, double*, Scalars*, int,            \
                                     cudaStream_t);                                             \
   template void launch_detach<T>(const Plan&, Fields<T>, double*, Scalars*, int, cudaStream_t); \

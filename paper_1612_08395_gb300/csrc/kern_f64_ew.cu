@@ -1,5 +1,6 @@
 // FP64 instantiation of the elementwise kernels and the FP64 helpers of the
 // refinement sweep, twiddle and index tables.
+#include <algorithm>
 #include "conv_kernels.cuh"
 
 namespace bem {
@@ -95,6 +96,51 @@ __global__ void k_geo_tables(int* so, int* sp, Geo g, int esize) {
 }
 void launch_geo_tables(int* so, int* sp, Geo g, int esize, cudaStream_t s) {
   k_geo_tables<<<32, 256, 0, s>>>(so, sp, g, esize);
+}
+
+// Bounding box of the contact set: first/last row and column holding an
+// element of S (atomicMin / atomicMax on sc->band0/band1/col0/col1, which start
+// at ny / -1 / nx / -1).
+__global__ void k_box(int nx, int ny, const uint8_t* S, Scalars* sc) {
+  __shared__ int lo, hi, clo, chi;
+  if (threadIdx.x == 0) { lo = ny; hi = -1; clo = nx; chi = -1; }
+  __syncthreads();
+  const bool vec = (nx & 15) == 0 && (reinterpret_cast<uintptr_t>(S) & 15) == 0;
+  int cmin = nx, cmax = -1;
+  for (int row = blockIdx.x; row < ny; row += gridDim.x) {  // the same trip count in every thread
+    const uint8_t* r = S + (size_t)row * nx;
+    bool any = false;
+    if (vec) {
+      const uint4* r4 = reinterpret_cast<const uint4*>(r);
+      for (int j = threadIdx.x; j < (nx >> 4); j += blockDim.x) {
+        const uint4 v = r4[j];
+        if ((v.x | v.y | v.z | v.w) != 0u) {
+          any = true;
+          for (int q = 0; q < 16; ++q)
+            if (r[16 * j + q]) { cmin = min(cmin, 16 * j + q); cmax = max(cmax, 16 * j + q); }
+        }
+      }
+    } else {
+      for (int j = threadIdx.x; j < nx; j += blockDim.x)
+        if (r[j]) { any = true; cmin = min(cmin, j); cmax = max(cmax, j); }
+    }
+    if (__syncthreads_or(any) && threadIdx.x == 0) {
+      lo = min(lo, row);
+      hi = max(hi, row);
+    }
+  }
+  if (cmax >= 0) { atomicMin(&clo, cmin); atomicMax(&chi, cmax); }
+  __syncthreads();
+  if (threadIdx.x == 0 && hi >= 0) {
+    atomicMin(&sc->band0, lo);
+    atomicMax(&sc->band1, hi);
+    atomicMin(&sc->col0, clo);
+    atomicMax(&sc->col1, chi);
+  }
+}
+void launch_box(const Plan& pl, const uint8_t* S, Scalars* sc, cudaStream_t s) {
+  const int grid = std::min(pl.ny, 2 * pl.nsm);
+  k_box<<<grid, 256, 0, s>>>(pl.nx, pl.ny, S, sc);
 }
 
 __global__ void k_active_set(const double* p, const double* g, uint8_t* S, size_t n) {

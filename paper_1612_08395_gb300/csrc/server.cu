@@ -48,6 +48,7 @@ size_t footprint(int nx, int ny) {
   b += 5 * 4 * n + 5 * 8 * n;           // FP32 and FP64 CG fields
   b += 16 * (M + 1) * py;               // spectrum set-up workspace
   b += 1 << 20;                         // partial sums, statistics, scalars
+  b += b / 3;                           // contact-box sub-contexts (tori of 1/4, 1/16, ... the area)
   return b;
 }
 

@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <mutex>
+#include <vector>
 #include <string>
 
 #include "bem.h"
@@ -158,7 +159,16 @@ struct bem_ctx {
   cudaEvent_t ev[2][4] = {};    // [pk/cg][A start, B start, C start, C end]
   double pass_ms[3] = {0, 0, 0};
   long long pass_count[2] = {0, 0};
+  double pass_bytes[3] = {0, 0, 0};  // algorithmic bytes / flops of the timed launches
+  double pass_flops[3] = {0, 0, 0};
+  // Contact-box sub-contexts (smaller tori for fixed-set solves whose contact
+  // set fits a box of at most half their size); they share the parent's stream.
+  bool is_sub = false, own_stream = true;
+  std::vector<bem_ctx*> subs;
 };
+
+static int create_ctx(int Nx, int Ny, double dx, double dy, double k, double nu, double E0, double c0,
+                      bem_ctx* parent, bem_ctx** out);
 
 namespace {
 
@@ -273,6 +283,10 @@ int init_scalars(bem_ctx* h, double tol, int max_iter, double pcrit) {
   s.delta = 0.0;
   s.bnorm = 1.0;
   s.pcrit = pcrit;
+  s.band0 = h->ny;  // empty box until k_box runs
+  s.band1 = -1;
+  s.col0 = h->nx;
+  s.col1 = -1;
   s.kerr = h->sc_host->kerr;
   *h->sc_host = s;
   // every member but the sticky error word
@@ -316,6 +330,7 @@ int capture(bem_ctx* h, bool pk, bool timed, cudaGraphExec_t* out) {
   CK(cudaGetLastError());
   CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
   PassArgs<T> a = make_args<T>(h);
+  a.use_band = pk ? 0 : 1;  // fixed-set CG: only the contact band's rows
   Fields<T> f = a.f;
   for (int it = 0; it < kChunk; ++it) {
     const bool mark = timed && it == 0;
@@ -352,7 +367,24 @@ int capture(bem_ctx* h, bool pk, bool timed, cudaGraphExec_t* out) {
 }
 
 // Run chunks of the captured loop until the device sets `done`.
-int run_loop(bem_ctx* h, cudaGraphExec_t g, int max_iter, bool pk) {
+// Algorithmic bytes and flops of one launch of each pass (A, B, C) on `rows`
+// grid rows, for element size es: field reads and writes of the mode, W
+// written / read / rewritten, the spectrum quarter; FFT flops 5 L log2 L per
+// complex transform of length L, halved for a pruned half.
+void add_pass_work(bem_ctx* h, bool pk, int rows, int es) {
+  const double nx = h->nx, M = h->px / 2, P = h->py, cx = 2.0 * es;
+  const double W = cx * (M + 1) * rows;
+  const double fa = pk ? 4.0 * es : 3.0 * es + 1, fc = pk ? 3.0 * es : 2.0 * es + 1;
+  h->pass_bytes[0] += fa * nx * rows + W;
+  h->pass_bytes[1] += 2 * W + es * (M + 1) * (P / 2 + 1);
+  h->pass_bytes[2] += W + fc * nx * rows;
+  const double fm = 5 * M * log2(M), fp = 5 * P * log2(P);
+  h->pass_flops[0] += rows * (0.5 * fm + 20 * M);
+  h->pass_flops[1] += (M + 1) * (fp + 8 * P);
+  h->pass_flops[2] += rows * (0.5 * fm + 20 * M);
+}
+
+int run_loop(bem_ctx* h, cudaGraphExec_t g, int max_iter, bool pk, int es) {
   const int max_launch = max_iter / kChunk + 2;
   for (int l = 0; l < max_launch; ++l) {
     CK(cudaGraphLaunch(g, h->stream));
@@ -366,7 +398,13 @@ int run_loop(bem_ctx* h, cudaGraphExec_t g, int max_iter, bool pk) {
         h->pass_ms[i] += ms;
       }
       h->pass_count[0] += 1;
-      if (!pk) h->pass_count[1] += 1;
+      int rows = h->ny;
+      if (!pk) {
+        h->pass_count[1] += 1;
+        const int b0 = h->sc_host->band0, b1 = h->sc_host->band1;
+        rows = b1 >= b0 ? b1 - b0 + 1 : 0;
+      }
+      add_pass_work(h, pk, rows, es);
     }
     if (h->sc_host->done) return BEM_OK;
   }
@@ -397,10 +435,74 @@ int run_pk(bem_ctx* h, double d, double tol, int max_iter, bool warm, StepOut* s
   launch_pk_init<T>(plan_of<T>(h), h->h64, d, pf.c, pf.p, pf.t, warm ? 1 : 0, h->ew_ngrid, h->stream);
   h->launches += 1;
   CKR(init_scalars(h, tol, max_iter, 0.0));
-  CKR(run_loop(h, pf.pk_graph[tg], max_iter, true));
+  CKR(run_loop(h, pf.pk_graph[tg], max_iter, true, (int)sizeof(T)));
   so->iterations += h->sc_host->iter;
   so->eps = h->sc_host->eps;
   if (h->sc_host->status != SC_OK) so->status = map_status(h->sc_host->status);
+  return BEM_OK;
+}
+
+// The sub-context whose torus is the smallest power-of-two size holding the
+// contact box twice over in each direction (so the zero padding of the box is
+// at least as large as the box, as the method's padding of the whole grid is),
+// or null when that is not smaller than this context's torus.  Created on
+// first use: its influence coefficients are the sub-table of this context's
+// (they depend only on the element offsets), its spectrum is its own.
+int pick_sub(bem_ctx* h, bem_ctx** out) {
+  *out = nullptr;
+  const Scalars& s = *h->sc_host;
+  if (s.band1 < s.band0 || s.col1 < s.col0) return BEM_OK;
+  const int bw = s.col1 - s.col0 + 1, bh = s.band1 - s.band0 + 1;
+  const int qx = pow2_at_least(2 * bw < 32 ? 32 : 2 * bw), qy = pow2_at_least(2 * bh < 32 ? 32 : 2 * bh);
+  if (qx > h->px || qy > h->py || (size_t)qx * qy >= (size_t)h->px * h->py) return BEM_OK;
+  for (bem_ctx* c : h->subs)
+    if (c->px == qx && c->py == qy) { *out = c; return BEM_OK; }
+  bem_ctx* c = nullptr;
+  CKR(create_ctx(qx / 2, qy / 2, h->dx, h->dy, h->k, h->nu, h->E0, h->c0, h, &c));
+  h->subs.push_back(c);
+  *out = c;
+  return BEM_OK;
+}
+
+template <typename T>
+int run_fixed_cg(bem_ctx* h, double tol, int max_iter, double pcrit, StepOut* so);
+
+// The fixed-set solve on the contact box: the operator restricted to S only
+// couples elements of S, all inside the box, so solving on a sub-grid placed
+// at the box origin (with the same element size and coefficients) gives the
+// same result as solving on the whole grid.  p outside S is zero either way.
+template <typename T>
+int fixed_cg_in_box(bem_ctx* h, bem_ctx* sub, double tol, int max_iter, double pcrit, StepOut* so) {
+  const int x0 = h->sc_host->col0, y0 = h->sc_host->band0;
+  PrecFields<T>& pf = fields_of<T>(h);
+  CKR(ensure_fields<T>(sub));
+  PrecFields<T>& bf = fields_of<T>(sub);
+  launch_mask_field<T>(pf.p, h->S, (size_t)h->nx * h->ny, h->stream);
+  launch_box_gather<T>(pf.p, pf.c, h->S, h->nx, h->ny, x0, y0, bf.p, bf.c, sub->S, sub->nx, sub->ny, h->stream);
+  sub->timing = h->timing;
+  StepOut bo;
+  const int rc = run_fixed_cg<T>(sub, tol, max_iter, pcrit, &bo);
+  if (rc != BEM_OK) return rc;
+  launch_box_scatter<T>(bf.p, pf.p, h->nx, h->ny, x0, y0, sub->nx, sub->ny, h->stream);
+  h->launches += 3 + sub->launches;
+  sub->launches = 0;
+  for (int i = 0; i < 3; ++i) {
+    h->pass_ms[i] += sub->pass_ms[i];
+    h->pass_bytes[i] += sub->pass_bytes[i];
+    h->pass_flops[i] += sub->pass_flops[i];
+    sub->pass_ms[i] = sub->pass_bytes[i] = sub->pass_flops[i] = 0;
+  }
+  h->pass_count[0] += sub->pass_count[0];
+  h->pass_count[1] += sub->pass_count[1];
+  sub->pass_count[0] = sub->pass_count[1] = 0;
+  // the solve's outcome, as the caller reads it from this context
+  h->sc_host->iter = sub->sc_host->iter;
+  h->sc_host->eps = sub->sc_host->eps;
+  h->sc_host->status = sub->sc_host->status;
+  h->sc_host->done = sub->sc_host->done;
+  so->iterations += bo.iterations;
+  so->eps = bo.eps;
+  if (bo.status != BEM_OK) so->status = bo.status;
   return BEM_OK;
 }
 
@@ -410,8 +512,16 @@ int run_fixed_cg(bem_ctx* h, double tol, int max_iter, double pcrit, StepOut* so
   CKR(ensure_fields<T>(h));
   PrecFields<T>& pf = fields_of<T>(h);
   const int tg = h->timing ? 1 : 0;
-  if (!pf.cg_graph[tg]) CKR(capture<T>(h, false, h->timing, &pf.cg_graph[tg]));
   CKR(init_scalars(h, tol, max_iter, pcrit));
+  launch_box(plan_of<T>(h), h->S, h->sc, h->stream);
+  h->launches += 1;
+  if (!h->is_sub) {
+    CKR(read_scalars(h));
+    bem_ctx* sub = nullptr;
+    CKR(pick_sub(h, &sub));
+    if (sub) return fixed_cg_in_box<T>(h, sub, tol, max_iter, pcrit, so);
+  }
+  if (!pf.cg_graph[tg]) CKR(capture<T>(h, false, h->timing, &pf.cg_graph[tg]));
   const size_t n = (size_t)h->nx * h->ny;
   launch_mask_field<T>(pf.p, h->S, n, h->stream);
   launch_mask_field<T>(pf.t, h->S, n, h->stream);
@@ -422,7 +532,7 @@ int run_fixed_cg(bem_ctx* h, double tol, int max_iter, double pcrit, StepOut* so
   launch_pass_c<T>(a, C_CG_G, h->stream);
   h->launches += 5;
   CKR(read_scalars(h));
-  if (!h->sc_host->done) CKR(run_loop(h, pf.cg_graph[tg], max_iter, false));
+  if (!h->sc_host->done) CKR(run_loop(h, pf.cg_graph[tg], max_iter, false, (int)sizeof(T)));
   so->iterations += h->sc_host->iter;
   so->eps = h->sc_host->eps;
   if (h->sc_host->status != SC_OK) so->status = map_status(h->sc_host->status);
@@ -536,6 +646,14 @@ extern "C" int bem_create(int Nx, int Ny, double dx, double dy, double k, double
                           double c0, bem_handle* out) {
   g_err.clear();
   if (!out) return fail(BEM_EINVAL, "out must not be NULL");
+  return create_ctx(Nx, Ny, dx, dy, k, nu, E0, c0, nullptr, out);
+}
+
+// A context for an Nx x Ny grid.  With a parent (a contact-box sub-context of
+// it): the parent's stream, and the influence coefficients copied from the
+// parent's table (offsets 0..Px/2 x 0..Py/2 of this torus are a sub-block).
+static int create_ctx(int Nx, int Ny, double dx, double dy, double k, double nu, double E0, double c0,
+                      bem_ctx* parent, bem_ctx** out) {
   if (Nx < 2 || Ny < 2 || Nx > 4096 || Ny > 4096)
     return fail(BEM_EINVAL, "grid %dx%d outside 2..4096", Nx, Ny);
   if (!(dx > 0) || !(dy > 0)) return fail(BEM_EINVAL, "element sizes must be > 0");
@@ -548,8 +666,13 @@ extern "C" int bem_create(int Nx, int Ny, double dx, double dy, double k, double
   bem_ctx* h = new bem_ctx();
   auto cleanup = [&](int rc) { bem_destroy(h); return rc; };
   if (cudaGetDevice(&h->device) != cudaSuccess) return cleanup(fail(BEM_ECUDA, "no CUDA device"));
-  if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess)
+  if (parent) {
+    h->is_sub = true;
+    h->own_stream = false;
+    h->stream = parent->stream;
+  } else if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
     return cleanup(fail(BEM_ECUDA, "stream creation failed"));
+  }
   {
     // once per device and process: shared-memory opt-ins and quadrature nodes
     static std::mutex init_mu;
@@ -628,7 +751,14 @@ extern "C" int bem_create(int Nx, int Ny, double dx, double dy, double k, double
   launch_twiddles(h->tw64 + M, h->tw32 + M, ilog2(h->py), h->stream);
   launch_split_twiddles(h->tw64 + M + h->py, h->tw32 + M + h->py, M, h->stream);
   // a1: influence coefficients on the offsets 0..Px/2, 0..Py/2 (Eq. 9)
-  launch_influence(h->kq64, M + 1, hyq, dx, dy, k, h->stream);
+  if (parent) {
+    const size_t pw = (size_t)parent->px / 2 + 1;
+    if (cudaMemcpy2DAsync(h->kq64, sizeof(double) * (M + 1), parent->kq64, sizeof(double) * pw,
+                          sizeof(double) * (M + 1), hyq, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+      return cleanup(fail(BEM_ECUDA, "influence sub-table copy failed"));
+  } else {
+    launch_influence(h->kq64, M + 1, hyq, dx, dy, k, h->stream);
+  }
   // spectrum of the even torus extension (Eq. 13: FFT(K)), FP64, once
   {
     void* Wspec = nullptr;
@@ -662,6 +792,8 @@ extern "C" int bem_create(int Nx, int Ny, double dx, double dy, double k, double
 extern "C" void bem_destroy(bem_handle h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  for (bem_ctx* c : h->subs) bem_destroy(c);
+  h->subs.clear();
   auto fr = [](void* p) { if (p) cudaFree(p); };
   for (int t = 0; t < 2; ++t)
     for (cudaGraphExec_t g : {h->f32.pk_graph[t], h->f32.cg_graph[t], h->f64.pk_graph[t], h->f64.cg_graph[t]})
@@ -675,7 +807,7 @@ extern "C" void bem_destroy(bem_handle h) {
   fr(h->f64.p); fr(h->f64.g); fr(h->f64.t); fr(h->f64.r); fr(h->f64.c);
   if (h->sc_host) cudaFreeHost(h->sc_host);
   if (h->stats_host) cudaFreeHost(h->stats_host);
-  if (h->stream) cudaStreamDestroy(h->stream);
+  if (h->stream && h->own_stream) cudaStreamDestroy(h->stream);
   delete h;
 }
 
@@ -684,6 +816,7 @@ extern "C" int bem_get_info(bem_handle h, bem_info* info) {
   info->Nx = h->nx; info->Ny = h->ny; info->Px = h->px; info->Py = h->py;
   info->dx = h->dx; info->dy = h->dy; info->k = h->k; info->nu = h->nu; info->E0 = h->E0; info->c0 = h->c0;
   info->alpha = h->alpha; info->compliance = h->A; info->device_bytes = h->bytes;
+  for (const bem_ctx* c : h->subs) info->device_bytes += c->bytes;
   info->kernel_launches = h->launches;
   return BEM_OK;
 }
@@ -703,6 +836,17 @@ extern "C" int bem_set_material(bem_handle h, double nu, double E0, double c0) {
     for (cudaGraphExec_t* g : {&h->f32.pk_graph[t], &h->f32.cg_graph[t], &h->f64.pk_graph[t], &h->f64.cg_graph[t]})
       if (*g) { cudaGraphExecDestroy(*g); *g = nullptr; }
   }
+  for (bem_ctx* c : h->subs) CKR(bem_set_material(c, nu, E0, c0));
+  return BEM_OK;
+}
+
+extern "C" int bem_pass_work(bem_handle h, double bytes[3], double flops[3]) {
+  if (!h || !bytes || !flops) return fail(BEM_EINVAL, "NULL argument");
+  const double n = h->pass_count[0] > 0 ? (double)h->pass_count[0] : 1.0;
+  for (int i = 0; i < 3; ++i) {
+    bytes[i] = h->pass_bytes[i] / n;
+    flops[i] = h->pass_flops[i] / n;
+  }
   return BEM_OK;
 }
 
@@ -714,6 +858,7 @@ extern "C" int bem_pass_times(bem_handle h, double ms[3], long long count[2], in
   if (reset) {
     for (int i = 0; i < 3; ++i) h->pass_ms[i] = 0;
     h->pass_count[0] = h->pass_count[1] = 0;
+    for (int i = 0; i < 3; ++i) h->pass_bytes[i] = h->pass_flops[i] = 0;
   }
   return BEM_OK;
 }
