@@ -128,6 +128,9 @@ template <typename T> void launch_pk_init(const Plan& pl, const double* h64, dou
 template <typename T> void launch_cg_update(const Plan& pl, Fields<T> f, double* part, Scalars* sc,
                                             int ngrid, cudaStream_t s);
 void launch_box(const Plan& pl, const uint8_t* S, Scalars* sc, cudaStream_t s);
+void launch_box_overlap(const Plan& pl, const double* h, double d, Scalars* sc, cudaStream_t s);
+void launch_box_copy64(const double* src, int nx, int ny, int x0, int y0, double* dst, int bx, int by,
+                       double fill, cudaStream_t s);
 // Copy the box [x0, x0+bx) x [y0, y0+by) of the nx x ny fields p, c, S into
 // bx x by sub-grid fields (zero where the box leaves the grid), and back for p.
 template <typename T> void launch_box_gather(const T* p, const T* c, const uint8_t* S, int nx, int ny, int x0,

@@ -138,6 +138,54 @@ __global__ void k_box(int nx, int ny, const uint8_t* S, Scalars* sc) {
     atomicMax(&sc->col1, chi);
   }
 }
+// Bounding box of the geometric overlap set {h <= d} (into sc->band0/band1/
+// col0/col1, which start at ny / -1 / nx / -1).
+__global__ void k_box_overlap(int nx, int ny, const double* __restrict__ h, double d, Scalars* sc) {
+  __shared__ int lo, hi, clo, chi;
+  if (threadIdx.x == 0) { lo = ny; hi = -1; clo = nx; chi = -1; }
+  __syncthreads();
+  int cmin = nx, cmax = -1;
+  for (int row = blockIdx.x; row < ny; row += gridDim.x) {  // the same trip count in every thread
+    const double* r = h + (size_t)row * nx;
+    bool any = false;
+    for (int j = threadIdx.x; j < nx; j += blockDim.x)
+      if (r[j] <= d) { any = true; cmin = min(cmin, j); cmax = max(cmax, j); }
+    if (__syncthreads_or(any) && threadIdx.x == 0) {
+      lo = min(lo, row);
+      hi = max(hi, row);
+    }
+  }
+  if (cmax >= 0) { atomicMin(&clo, cmin); atomicMax(&chi, cmax); }
+  __syncthreads();
+  if (threadIdx.x == 0 && hi >= 0) {
+    atomicMin(&sc->band0, lo);
+    atomicMax(&sc->band1, hi);
+    atomicMin(&sc->col0, clo);
+    atomicMax(&sc->col1, chi);
+  }
+}
+void launch_box_overlap(const Plan& pl, const double* h, double d, Scalars* sc, cudaStream_t s) {
+  const int grid = std::min(pl.ny, 2 * pl.nsm);
+  k_box_overlap<<<grid, 256, 0, s>>>(pl.nx, pl.ny, h, d, sc);
+}
+
+// Copy the box [x0, x0+bx) x [y0, y0+by) of an nx x ny FP64 field, `fill` where
+// the box leaves the grid (bx a power of two).
+__global__ void k_box_copy64(const double* __restrict__ src, int nx, int ny, int x0, int y0,
+                             double* __restrict__ dst, int lbx, int nb, double fill) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x) {
+    const int X = x0 + (i & ((1 << lbx) - 1)), Y = y0 + (i >> lbx);
+    dst[i] = (X < nx && Y < ny) ? src[(size_t)Y * nx + X] : fill;
+  }
+}
+void launch_box_copy64(const double* src, int nx, int ny, int x0, int y0, double* dst, int bx, int by,
+                       double fill, cudaStream_t s) {
+  int lbx = 0;
+  while ((1 << lbx) < bx) ++lbx;
+  const int nb = bx * by;
+  k_box_copy64<<<ew_grid((size_t)nb), 256, 0, s>>>(src, nx, ny, x0, y0, dst, lbx, nb, fill);
+}
+
 void launch_box(const Plan& pl, const uint8_t* S, Scalars* sc, cudaStream_t s) {
   const int grid = std::min(pl.ny, 2 * pl.nsm);
   k_box<<<grid, 256, 0, s>>>(pl.nx, pl.ny, S, sc);

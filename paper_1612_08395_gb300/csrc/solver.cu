@@ -425,11 +425,24 @@ int map_status(int sc_status) {
   return BEM_OK;
 }
 
+int pick_sub(bem_ctx* h, bem_ctx** out);
+template <typename T>
+int pk_in_box(bem_ctx* h, bem_ctx* sub, double d, double tol, int max_iter, bool warm, StepOut* so);
+
 // Non-adhesive solve at depth d in precision T (Sec. 2.1, Polonsky-Keer CG).
 template <typename T>
 int run_pk(bem_ctx* h, double d, double tol, int max_iter, bool warm, StepOut* so) {
   CKR(ensure_fields<T>(h));
   PrecFields<T>& pf = fields_of<T>(h);
+  if (!h->is_sub) {
+    CKR(init_scalars(h, tol, max_iter, 0.0));
+    launch_box_overlap(plan_of<T>(h), h->h64, d, h->sc, h->stream);
+    h->launches += 1;
+    CKR(read_scalars(h));
+    bem_ctx* sub = nullptr;
+    CKR(pick_sub(h, &sub));
+    if (sub) return pk_in_box<T>(h, sub, d, tol, max_iter, warm, so);
+  }
   const int tg = h->timing ? 1 : 0;
   if (!pf.pk_graph[tg]) CKR(capture<T>(h, true, h->timing, &pf.pk_graph[tg]));
   launch_pk_init<T>(plan_of<T>(h), h->h64, d, pf.c, pf.p, pf.t, warm ? 1 : 0, h->ew_ngrid, h->stream);
@@ -466,6 +479,66 @@ int pick_sub(bem_ctx* h, bem_ctx** out) {
 
 template <typename T>
 int run_fixed_cg(bem_ctx* h, double tol, int max_iter, double pcrit, StepOut* so);
+template <typename T>
+int run_pk(bem_ctx* h, double d, double tol, int max_iter, bool warm, StepOut* so);
+
+// Move a sub-context's launch count, pass timings and work into this context,
+// and the solve's outcome into this context's host scalars.
+void absorb_sub(bem_ctx* h, bem_ctx* sub) {
+  h->launches += sub->launches;
+  sub->launches = 0;
+  for (int i = 0; i < 3; ++i) {
+    h->pass_ms[i] += sub->pass_ms[i];
+    h->pass_bytes[i] += sub->pass_bytes[i];
+    h->pass_flops[i] += sub->pass_flops[i];
+    sub->pass_ms[i] = sub->pass_bytes[i] = sub->pass_flops[i] = 0;
+  }
+  h->pass_count[0] += sub->pass_count[0];
+  h->pass_count[1] += sub->pass_count[1];
+  sub->pass_count[0] = sub->pass_count[1] = 0;
+  h->sc_host->iter = sub->sc_host->iter;
+  h->sc_host->eps = sub->sc_host->eps;
+  h->sc_host->status = sub->sc_host->status;
+  h->sc_host->done = sub->sc_host->done;
+}
+
+// The non-adhesive solve on the box of the geometric overlap set {h <= d}.
+// Pressures are non-negative and the influence coefficients positive, so the
+// deflection u = A K*p is non-negative and the gap u + h - d >= h - d: no
+// element with h > d can carry pressure.  The Polonsky-Keer iteration on a
+// sub-grid holding that set is therefore the iteration on the whole grid
+// (outside it p stays 0 and g > 0).  Sub-grid elements beyond the grid get a
+// height far above any depth.  Afterwards p is scattered back and the gap of
+// the whole grid is formed with one full transform.
+template <typename T>
+int pk_in_box(bem_ctx* h, bem_ctx* sub, double d, double tol, int max_iter, bool warm, StepOut* so) {
+  const int x0 = h->sc_host->col0, y0 = h->sc_host->band0;
+  const size_t n = (size_t)h->nx * h->ny;
+  PrecFields<T>& pf = fields_of<T>(h);
+  CKR(ensure_fields<T>(sub));
+  PrecFields<T>& bf = fields_of<T>(sub);
+  launch_box_copy64(h->h64, h->nx, h->ny, x0, y0, sub->h64, sub->nx, sub->ny, 1.0e6, h->stream);
+  launch_box_gather<T>(pf.p, pf.c, h->S, h->nx, h->ny, x0, y0, bf.p, bf.c, sub->S, sub->nx, sub->ny, h->stream);
+  h->launches += 2;
+  sub->timing = h->timing;
+  StepOut bo;
+  CKR(run_pk<T>(sub, d, tol, max_iter, warm, &bo));
+  CK(cudaMemsetAsync(pf.p, 0, n * sizeof(T), h->stream));
+  launch_box_scatter<T>(bf.p, pf.p, h->nx, h->ny, x0, y0, sub->nx, sub->ny, h->stream);
+  launch_offset<T>(h->h64, d, pf.c, n, h->stream);
+  PassArgs<T> a = make_args<T>(h);
+  a.f.src = pf.p;
+  a.sc = nullptr;
+  launch_pass_a<T>(a, A_PLAIN, h->stream);
+  launch_pass_b<T>(a, B_CONV, h->stream);
+  launch_pass_c<T>(a, C_GAP, h->stream);
+  h->launches += 5;
+  absorb_sub(h, sub);
+  so->iterations += bo.iterations;
+  so->eps = bo.eps;
+  if (bo.status != BEM_OK) so->status = bo.status;
+  return BEM_OK;
+}
 
 // The fixed-set solve on the contact box: the operator restricted to S only
 // couples elements of S, all inside the box, so solving on a sub-grid placed
@@ -484,22 +557,8 @@ int fixed_cg_in_box(bem_ctx* h, bem_ctx* sub, double tol, int max_iter, double p
   const int rc = run_fixed_cg<T>(sub, tol, max_iter, pcrit, &bo);
   if (rc != BEM_OK) return rc;
   launch_box_scatter<T>(bf.p, pf.p, h->nx, h->ny, x0, y0, sub->nx, sub->ny, h->stream);
-  h->launches += 3 + sub->launches;
-  sub->launches = 0;
-  for (int i = 0; i < 3; ++i) {
-    h->pass_ms[i] += sub->pass_ms[i];
-    h->pass_bytes[i] += sub->pass_bytes[i];
-    h->pass_flops[i] += sub->pass_flops[i];
-    sub->pass_ms[i] = sub->pass_bytes[i] = sub->pass_flops[i] = 0;
-  }
-  h->pass_count[0] += sub->pass_count[0];
-  h->pass_count[1] += sub->pass_count[1];
-  sub->pass_count[0] = sub->pass_count[1] = 0;
-  // the solve's outcome, as the caller reads it from this context
-  h->sc_host->iter = sub->sc_host->iter;
-  h->sc_host->eps = sub->sc_host->eps;
-  h->sc_host->status = sub->sc_host->status;
-  h->sc_host->done = sub->sc_host->done;
+  h->launches += 3;
+  absorb_sub(h, sub);
   so->iterations += bo.iterations;
   so->eps = bo.eps;
   if (bo.status != BEM_OK) so->status = bo.status;
