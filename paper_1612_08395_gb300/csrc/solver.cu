@@ -661,7 +661,7 @@ int max_abs_on_set(bem_ctx* h, const double* x, double* out) {
 // the FP32 fixed-set CG, and adds dp.  Non-adhesive: S = {p > 0} U {g < 0} and
 // p is projected onto p >= 0 after the update; adhesive: S is held and tension
 // is allowed.  Stops when max_S |g64| <= tol64 * max_S |h - d|.
-int refine(bem_ctx* h, double d, bool adhesive, int sweeps, double tol64, double tol32, StepOut* so) {
+int refine_here(bem_ctx* h, double d, bool adhesive, int sweeps, double tol64, double tol32, StepOut* so) {
   const size_t n = (size_t)h->nx * h->ny;
   for (int s = 0; s < sweeps; ++s) {
     CKR(gap64(h, d));
@@ -683,6 +683,38 @@ int refine(bem_ctx* h, double d, bool adhesive, int sweeps, double tol64, double
     h->launches += 1;
   }
   return BEM_OK;
+}
+
+// The refinement on the smallest torus holding the set it works on: the held
+// set S (adhesive: the residual matters only on S, and p vanishes off it) or
+// the overlap set {h <= d} (non-adhesive: the active set {p > 0} U {g < 0}
+// lies inside it, since g >= h - d).  The FP64 pressure, the profile and S
+// are gathered into the sub-context and the pressure is scattered back.
+int refine(bem_ctx* h, double d, bool adhesive, int sweeps, double tol64, double tol32, StepOut* so) {
+  if (!h->is_sub) {
+    CKR(init_scalars(h, 0.0, 0, 0.0));  // an empty box to collect into
+    if (adhesive) launch_box(h->plan64, h->S, h->sc, h->stream);
+    else launch_box_overlap(h->plan64, h->h64, d, h->sc, h->stream);
+    h->launches += 1;
+    CKR(read_scalars(h));
+    bem_ctx* sub = nullptr;
+    CKR(pick_sub(h, &sub));
+    if (sub) {
+      const int x0 = h->sc_host->col0, y0 = h->sc_host->band0;
+      CKR(ensure_fields<double>(sub));
+      CKR(ensure_fields<float>(sub));
+      launch_box_gather<double>(h->io64, h->io64, h->S, h->nx, h->ny, x0, y0, sub->io64, sub->io64b, sub->S,
+                                sub->nx, sub->ny, h->stream);
+      launch_box_copy64(h->h64, h->nx, h->ny, x0, y0, sub->h64, sub->nx, sub->ny, 1.0e6, h->stream);
+      sub->timing = h->timing;
+      CKR(refine_here(sub, d, adhesive, sweeps, tol64, tol32, so));
+      launch_box_scatter<double>(sub->io64, h->io64, h->nx, h->ny, x0, y0, sub->nx, sub->ny, h->stream);
+      h->launches += 3;
+      absorb_sub(h, sub);
+      return BEM_OK;
+    }
+  }
+  return refine_here(h, d, adhesive, sweeps, tol64, tol32, so);
 }
 
 int validate_ptr(const void* p, const char* name) {

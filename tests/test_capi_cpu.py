@@ -98,3 +98,10 @@ def test_server_footprint(bem_mod):
     # at least the FP32 and FP64 CG fields and the transposed half spectrum
     n = 1024
     assert f(n, n) > (4 + 8) * 5 * n * n + 16 * (n + 1) * n
+
+
+def test_library_resolves_all_symbols_at_load(bem_mod):
+    """Every internal symbol resolves when the library is loaded with immediate
+    binding (an uninstantiated template would fail here, not at first call)."""
+    import ctypes
+    ctypes.CDLL(bem_mod.LIB_PATH, mode=os.RTLD_NOW)
