@@ -66,7 +66,10 @@ static int fail(int code, const char* fmt, ...) {
 
 namespace {
 
-constexpr int kChunk = 8;  // CG iterations per captured graph launch
+#ifndef BEM_CHUNK
+#define BEM_CHUNK 8
+#endif
+constexpr int kChunk = BEM_CHUNK;  // CG iterations per captured graph launch
 
 // Threads per CTA of the row passes (rows per CTA x M/8); 512 keeps two CTAs
 // resident per SM at the passes' register use.

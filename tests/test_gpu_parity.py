@@ -237,3 +237,29 @@ def test_adhesive_rejects_bad_input(bem_mod, cuda_ok):
         with pytest.raises(bem_mod.BemError) as e:
             h.sweep(I.paraboloid(n), [0.01, 0.02], dgamma=1e-3)
         assert e.value.code == bem_mod.BEM_EINVAL
+
+
+# ------------------------------------------------------------------ work accounting
+def test_pass_work_full_torus_and_box(bem_mod, cuda_ok):
+    """bem_pass_work: a flat indenter pressed in everywhere keeps the full torus, so
+    pass B moves W (in and out) and the spectrum quarter; an adhesive paraboloid's
+    fixed-set solves run on the contact box's smaller torus and move less."""
+    n = 64
+    dx = 1.0 / n
+    px, py = torus_sizes(n, n)
+    M = px // 2
+    full_b = 2 * 8 * (M + 1) * n + 4 * (M + 1) * (py // 2 + 1)
+    with bem_mod.Handle(n, n, dx, dx, 0.3, 0.3) as h:
+        h.pass_times(reset=True)
+        res, rc = h.solve(np.zeros((n, n)), 1e-3, precision="fp32", time_passes=True)
+        (ba, bb, bc), (fa, fb, fc) = h.pass_work()
+        ms, cnt, cnt_cg = h.pass_times(reset=True)
+        assert cnt > 0 and cnt_cg == 0
+        assert bb == full_b
+        assert ba == 16 * n * n + 8 * (M + 1) * n and bc == 12 * n * n + 8 * (M + 1) * n
+        steps = np.linspace(0.01, -0.01, 21)
+        h.sweep(I.paraboloid(n), steps, dgamma=1e-3, precision="fp32", time_passes=True)
+        (ba2, bb2, bc2), _ = h.pass_work()
+        ms2, cnt2, cnt_cg2 = h.pass_times(reset=True)
+        assert cnt_cg2 > 0
+        assert bb2 < 0.5 * full_b
