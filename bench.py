@@ -423,6 +423,7 @@ def main():
         "dtype": "f32" if args.precision != "fp64" else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "precision": args.precision, "grid": [N, N],
                    "torus": [info.Px, info.Py], "parallelism": f"replicas x{world}",
+                   "fp32_shapes": {"rows_per_cta": info.rows_per_cta, "cols_per_cta": info.cols_per_cta},
                    "l2": "flushed between steps (256 MiB write)",
                    "cg_iterations_per_step": iters_total / args.steps,
                    "pull_off_force": min(forces), "last_contact_depth": float(ds[last_contact]),

@@ -82,7 +82,12 @@ typedef struct {
  *   Nx, Ny : 2..4096;  dx, dy > 0;  -1 < k < 1;  -1 < nu <= 0.5 with
  *   beta(k,nu)^2 > 0 (Eq. 4);  E0 > 0;  c0 > 0;  out != NULL.
  * The handle creates its own non-blocking stream on the current device.
- * Returns BEM_EINVAL, BEM_ENOMEM or BEM_ECUDA on failure (*out untouched). */
+ * Returns BEM_EINVAL, BEM_ENOMEM or BEM_ECUDA on failure (*out untouched).
+ * The first handle of each grid size in a process times a few launch shapes
+ * of the FP32 transform passes (rows per CTA of the row passes, columns per
+ * CTA of the column pass; a few milliseconds) and keeps the fastest for every
+ * later handle of that size (bem_get_info reports them).  BEM_AUTOTUNE=0 in
+ * the environment keeps the default shapes. */
 int bem_create(int Nx, int Ny, double dx, double dy, double k, double nu, double E0, double c0,
                bem_handle *out);
 
@@ -197,6 +202,8 @@ typedef struct {
   double compliance; /* A = alpha (1-nu^2) c0^k / E0 (Eq. 12)         */
   size_t device_bytes; /* device memory held by the handle            */
   unsigned long long kernel_launches; /* kernels launched by this handle so far */
+  int rows_per_cta;     /* FP32 row passes: grid rows per CTA            */
+  int cols_per_cta;     /* FP32 column pass: columns per CTA             */
 } bem_info;
 
 int bem_get_info(bem_handle h, bem_info *info);

@@ -6,8 +6,10 @@
 #include <stddef.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
+#include <map>
 #include <mutex>
 #include <vector>
 #include <string>
@@ -92,38 +94,62 @@ int pow2_at_least(int v) { int p = 1; while (p < v) p <<= 1; return p; }
 constexpr int kMinThreads = 64;
 constexpr int kCtasPerSm = 2;
 
-Plan make_plan(int nx, int ny, int px, int py, int esize, int nsm) {
+// The plan for given rows per CTA of the row passes (nbA) and columns per CTA
+// of the column pass (nbB).
+Plan plan_with(int nx, int ny, int px, int py, int esize, int nsm, int nbA, int nbB) {
   Plan pl{};
   pl.nx = nx; pl.ny = ny; pl.px = px; pl.py = py;
   pl.M = px / 2;
   const int logM = ilog2(pl.M), logPy = ilog2(py);
-  const int tr = pl.M / 8;
+  pl.nbA = nbA;
+  pl.lognbA = ilog2(nbA);
+  pl.gA = make_geo(logM, nbA, esize);
+  pl.threadsA = nbA * (pl.M / 8);
+  pl.gridA = (ny + nbA - 1) / nbA;
+  pl.smemA = (size_t)nbA * pl.gA.rs * 2 * esize;
+  pl.smemC = pl.smemA;
+  pl.nbB = nbB;
+  pl.gB = make_geo(logPy, nbB, esize);
+  pl.threadsB = nbB * (py / 8);
+  pl.gridB = (pl.M + 1 + nbB - 1) / nbB;
+  pl.smemB = (size_t)nbB * pl.gB.rs * 2 * esize;
+  pl.nsm = nsm;
+  return pl;
+}
+
+// Whether a plan's shapes are launchable: whole warps, the kernels' launch
+// bounds, and shared memory (with the persistent passes' staging) in budget.
+bool shape_fits(const Plan& pl, int esize) {
+  const int logM = ilog2(pl.M), logPy = ilog2(pl.py);
+  const int capA = logM >= 13 ? 1024 : 512, capB = logPy >= 13 ? 1024 : 512;
+  if (pl.nbA < 1 || pl.nbA > 64 || pl.nbB < 1 || pl.nbB > 64) return false;
+  if (pl.threadsA < 64 || pl.threadsA > capA || (pl.threadsA & 31)) return false;
+  if (pl.threadsB < 64 || pl.threadsB > capB || (pl.threadsB & 31)) return false;
+  const size_t lim = 200 * 1024, rows = (size_t)pl.nbA * pl.nx;
+  if (pl.smemA + (3 * (size_t)esize + 1) * rows + 16 > lim) return false;
+  if (pl.smemC + (size_t)2 * esize * (pl.M + 1) * pl.nbA + (2 * (size_t)esize + 1) * rows + 32 > lim) return false;
+  if (pl.smemB > lim) return false;
+  return true;
+}
+
+// Default shapes: about 256 threads per CTA, rows of W written in 32-byte
+// segments, and for small grids about two CTAs per SM.
+Plan make_plan(int nx, int ny, int px, int py, int esize, int nsm) {
+  const int M = px / 2;
+  const int tr = M / 8;
   int nb = 256 / tr;
   const int sector = 32 / (2 * esize);  // rows per CTA for 32-byte segments of W
   if (nb < sector) nb = sector;
   if (nb < 1) nb = 1;
   while (nb > 1 && nb * tr > BEM_MAX_THREADS_A) nb >>= 1;
-  while (nb > 1 && (size_t)nb * (pl.M + 32) * 2 * esize > 128 * 1024) nb >>= 1;
+  while (nb > 1 && (size_t)nb * (M + 32) * 2 * esize > 128 * 1024) nb >>= 1;
   while (nb > 1 && (nb / 2) * tr >= kMinThreads && (ny + nb - 1) / nb < kCtasPerSm * nsm) nb >>= 1;
-  pl.nbA = nb;
-  pl.lognbA = ilog2(nb);
-  pl.gA = make_geo(logM, nb, esize);
-  pl.threadsA = nb * tr;
-  pl.gridA = (ny + nb - 1) / nb;
-  pl.smemA = (size_t)nb * pl.gA.rs * 2 * esize;
-  pl.smemC = pl.smemA;
   const int tb = py / 8;
   int nbb = 256 / tb;
   if (nbb < 1) nbb = 1;
   while (nbb > 1 && (size_t)nbb * (py + 32) * 2 * esize > 128 * 1024) nbb >>= 1;
-  while (nbb > 1 && (nbb / 2) * tb >= kMinThreads && (pl.M + nbb) / nbb < kCtasPerSm * nsm) nbb >>= 1;
-  pl.nbB = nbb;
-  pl.gB = make_geo(logPy, nbb, esize);
-  pl.threadsB = nbb * tb;
-  pl.gridB = (pl.M + 1 + nbb - 1) / nbb;
-  pl.smemB = (size_t)nbb * pl.gB.rs * 2 * esize;
-  pl.nsm = nsm;
-  return pl;
+  while (nbb > 1 && (nbb / 2) * tb >= kMinThreads && (M + nbb) / nbb < kCtasPerSm * nsm) nbb >>= 1;
+  return plan_with(nx, ny, px, py, esize, nsm, nb, nbb);
 }
 
 }  // namespace
@@ -720,6 +746,102 @@ int refine(bem_ctx* h, double d, bool adhesive, int sweeps, double tol64, double
   return refine_here(h, d, adhesive, sweeps, tol64, tol32, so);
 }
 
+// ---------------------------------------------------------------------------
+// Launch-shape autotuner (FP32 passes).  The first context of each grid size
+// times the plain transform with the default shapes and with half and twice
+// the rows per CTA of the row passes and the columns per CTA of the column
+// pass, and keeps the fastest of each (a change needs a 3% gain, so timing
+// noise keeps the default).  The choice is kept for the process, and the lock
+// is held while timing, so every context of a size uses the same shapes.
+struct ShapeKey {
+  int nx, ny, px, py;
+  bool operator<(const ShapeKey& o) const {
+    return nx != o.nx ? nx < o.nx : ny != o.ny ? ny < o.ny : px != o.px ? px < o.px : py < o.py;
+  }
+};
+std::mutex g_tune_mu;
+std::map<ShapeKey, std::pair<int, int>> g_tuned;
+
+void set_plan32(bem_ctx* h, const Plan& pl) {
+  h->plan32 = pl;
+  int* g32 = h->geo;
+  const int M = h->px / 2;
+  launch_geo_tables(g32, g32 + kSoEntries, pl.gA, 4, h->stream);
+  launch_geo_tables(g32 + kSoEntries + M, g32 + 2 * kSoEntries + M, pl.gB, 4, h->stream);
+}
+
+// Device milliseconds of passes A, B, C (summed over `reps` plain transforms).
+int time_passes32(bem_ctx* h, int reps, double ms[3]) {
+  cudaEvent_t ev[4];
+  for (int i = 0; i < 4; ++i) CK(cudaEventCreate(&ev[i]));
+  ms[0] = ms[1] = ms[2] = 0;
+  PassArgs<float> a = make_args<float>(h);
+  a.f.src = h->f32.p;
+  a.f.dst = h->f32.g;
+  a.sc = nullptr;
+  int rc = BEM_OK;
+  for (int it = 0; it < reps + 2 && rc == BEM_OK; ++it) {  // two untimed warm-up transforms
+    cudaEventRecord(ev[0], h->stream);
+    launch_pass_a<float>(a, A_PLAIN, h->stream);
+    cudaEventRecord(ev[1], h->stream);
+    launch_pass_b<float>(a, B_CONV, h->stream);
+    cudaEventRecord(ev[2], h->stream);
+    launch_pass_c<float>(a, C_PLAIN, h->stream);
+    cudaEventRecord(ev[3], h->stream);
+    if (cudaEventSynchronize(ev[3]) != cudaSuccess) { rc = BEM_ECUDA; break; }
+    if (it < 2) continue;
+    for (int i = 0; i < 3; ++i) {
+      float t = 0;
+      cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
+      ms[i] += t;
+    }
+  }
+  for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
+  if (rc != BEM_OK) return fail(rc, "autotuner timing failed: %s", cudaGetErrorString(cudaGetLastError()));
+  h->launches += 3 * (unsigned long long)(reps + 2);
+  return BEM_OK;
+}
+
+int autotune32(bem_ctx* h) {
+  const char* env = getenv("BEM_AUTOTUNE");
+  if (env && env[0] == '0') return BEM_OK;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  const ShapeKey key{h->nx, h->ny, h->px, h->py};
+  const Plan base = h->plan32;
+  auto it = g_tuned.find(key);
+  if (it != g_tuned.end()) {
+    if (it->second.first != base.nbA || it->second.second != base.nbB)
+      set_plan32(h, plan_with(h->nx, h->ny, h->px, h->py, 4, base.nsm, it->second.first, it->second.second));
+    return BEM_OK;
+  }
+  CKR(ensure_fields<float>(h));
+  constexpr int reps = 6;
+  double t0[3];
+  CKR(time_passes32(h, reps, t0));
+  int bestA = base.nbA, bestB = base.nbB;
+  double tAC = t0[0] + t0[2], tB = t0[1];
+  for (int nb : {base.nbA / 2, base.nbA * 2}) {
+    const Plan pl = plan_with(h->nx, h->ny, h->px, h->py, 4, base.nsm, nb, base.nbB);
+    if (nb < 1 || !shape_fits(pl, 4)) continue;
+    set_plan32(h, pl);
+    double t[3];
+    CKR(time_passes32(h, reps, t));
+    if (t[0] + t[2] < 0.97 * tAC) { tAC = t[0] + t[2]; bestA = nb; }
+  }
+  for (int nb : {base.nbB / 2, base.nbB * 2}) {
+    const Plan pl = plan_with(h->nx, h->ny, h->px, h->py, 4, base.nsm, base.nbA, nb);
+    if (nb < 1 || !shape_fits(pl, 4)) continue;
+    set_plan32(h, pl);
+    double t[3];
+    CKR(time_passes32(h, reps, t));
+    if (t[1] < 0.97 * tB) { tB = t[1]; bestB = nb; }
+  }
+  set_plan32(h, plan_with(h->nx, h->ny, h->px, h->py, 4, base.nsm, bestA, bestB));
+  CK(cudaStreamSynchronize(h->stream));
+  g_tuned[key] = {bestA, bestB};
+  return BEM_OK;
+}
+
 int validate_ptr(const void* p, const char* name) {
   if (!p) return fail(BEM_EINVAL, "%s must not be NULL", name);
   return BEM_OK;
@@ -815,7 +937,7 @@ static int create_ctx(int Nx, int Ny, double dx, double dy, double k, double nu,
   if ((rc = dmalloc(h, (void**)&h->io64, sizeof(double) * n))) return cleanup(rc);
   if ((rc = dmalloc(h, (void**)&h->io64b, sizeof(double) * n))) return cleanup(rc);
   if ((rc = dmalloc(h, (void**)&h->S, n))) return cleanup(rc);
-  const int gmax = (h->plan32.gridA > h->plan64.gridA ? h->plan32.gridA : h->plan64.gridA);
+  const int gmax = Ny;  // per-CTA partials come from row groups: at most one per row, for any shape
   if ((rc = dmalloc(h, (void**)&h->part, sizeof(double) * 4 * (size_t)gmax))) return cleanup(rc);
   if ((rc = dmalloc(h, (void**)&h->partC, sizeof(double) * 4 * (size_t)gmax))) return cleanup(rc);
   h->ew_ngrid = (int)((n + 255) / 256 < 152 * 8 ? (n + 255) / 256 : 152 * 8);
@@ -879,6 +1001,7 @@ static int create_ctx(int Nx, int Ny, double dx, double dy, double k, double nu,
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cleanup(fail(BEM_ECUDA, "set-up kernels failed: %s", cudaGetErrorString(e)));
+  if ((rc = autotune32(h))) return cleanup(rc);
   *out = h;
   return BEM_OK;
 }
@@ -910,6 +1033,8 @@ extern "C" int bem_get_info(bem_handle h, bem_info* info) {
   info->Nx = h->nx; info->Ny = h->ny; info->Px = h->px; info->Py = h->py;
   info->dx = h->dx; info->dy = h->dy; info->k = h->k; info->nu = h->nu; info->E0 = h->E0; info->c0 = h->c0;
   info->alpha = h->alpha; info->compliance = h->A; info->device_bytes = h->bytes;
+  info->rows_per_cta = h->plan32.nbA;
+  info->cols_per_cta = h->plan32.nbB;
   for (const bem_ctx* c : h->subs) info->device_bytes += c->bytes;
   info->kernel_launches = h->launches;
   return BEM_OK;
