@@ -500,7 +500,13 @@ int pick_sub(bem_ctx* h, bem_ctx** out) {
   for (bem_ctx* c : h->subs)
     if (c->px == qx && c->py == qy) { *out = c; return BEM_OK; }
   bem_ctx* c = nullptr;
-  CKR(create_ctx(qx / 2, qy / 2, h->dx, h->dy, h->k, h->nu, h->E0, h->c0, h, &c));
+  if (create_ctx(qx / 2, qy / 2, h->dx, h->dy, h->k, h->nu, h->E0, h->c0, h, &c) != BEM_OK) {
+    // no room for the smaller torus (or it failed to set up): the whole grid gives
+    // the same result, so carry on there
+    g_err.clear();
+    cudaGetLastError();
+    return BEM_OK;
+  }
   h->subs.push_back(c);
   *out = c;
   return BEM_OK;
