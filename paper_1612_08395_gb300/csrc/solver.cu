@@ -68,6 +68,10 @@ static int fail(int code, const char* fmt, ...) {
 
 namespace {
 
+// CTAs per SM of the grid-stride elementwise kernels (CG update, statistics, detach)
+#ifndef BEM_EW_CTAS_PER_SM
+#define BEM_EW_CTAS_PER_SM 2
+#endif
 #ifndef BEM_CHUNK
 #define BEM_CHUNK 8
 #endif
@@ -946,7 +950,8 @@ static int create_ctx(int Nx, int Ny, double dx, double dy, double k, double nu,
   const int gmax = Ny;  // per-CTA partials come from row groups: at most one per row, for any shape
   if ((rc = dmalloc(h, (void**)&h->part, sizeof(double) * 4 * (size_t)gmax))) return cleanup(rc);
   if ((rc = dmalloc(h, (void**)&h->partC, sizeof(double) * 4 * (size_t)gmax))) return cleanup(rc);
-  h->ew_ngrid = (int)((n + 255) / 256 < 152 * 8 ? (n + 255) / 256 : 152 * 8);
+  h->ew_ngrid = (int)((n + 255) / 256 < (size_t)BEM_EW_CTAS_PER_SM * h->plan32.nsm
+                          ? (n + 255) / 256 : (size_t)BEM_EW_CTAS_PER_SM * h->plan32.nsm);
   if (h->ew_ngrid < 1) h->ew_ngrid = 1;
   if ((rc = dmalloc(h, (void**)&h->partE, sizeof(double) * 4 * (size_t)h->ew_ngrid))) return cleanup(rc);
   h->stats_ngrid = h->ew_ngrid;
