@@ -46,7 +46,8 @@ extern "C" {
 #define BEM_PREC_FP32_REFINE 2
 
 /* Record CUDA events around the three transform passes of the first CG
- * iteration of every captured chunk (read back with bem_pass_times). */
+ * iteration of every fourth captured chunk of 8 iterations, the first chunk of
+ * every solve included (read back with bem_pass_times). */
 #define BEM_FLAG_TIME_PASSES 1
 
 typedef struct bem_ctx *bem_handle;

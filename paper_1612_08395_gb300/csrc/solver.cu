@@ -417,13 +417,19 @@ void add_pass_work(bem_ctx* h, bool pk, int rows, int es) {
   h->pass_flops[2] += rows * (0.5 * fm + 20 * M);
 }
 
-int run_loop(bem_ctx* h, cudaGraphExec_t g, int max_iter, bool pk, int es) {
+// Under BEM_FLAG_TIME_PASSES every kTimeEvery-th chunk (the first of each
+// solve included) runs the graph with event-record nodes; the others run the
+// plain graph, so the sampling costs little of the time it measures.
+constexpr int kTimeEvery = 4;
+
+int run_loop(bem_ctx* h, cudaGraphExec_t g, cudaGraphExec_t g_timed, int max_iter, bool pk, int es) {
   const int max_launch = max_iter / kChunk + 2;
   for (int l = 0; l < max_launch; ++l) {
-    CK(cudaGraphLaunch(g, h->stream));
+    const bool timed = h->timing && l % kTimeEvery == 0;
+    CK(cudaGraphLaunch(timed ? g_timed : g, h->stream));
     h->launches += (unsigned long long)kChunk * (pk ? 6 : 4);
     CKR(read_scalars(h));
-    if (h->timing) {
+    if (timed) {
       cudaEvent_t* ev = h->ev[pk ? 0 : 1];
       for (int i = 0; i < 3; ++i) {
         float ms = 0;
@@ -476,12 +482,12 @@ int run_pk(bem_ctx* h, double d, double tol, int max_iter, bool warm, StepOut* s
     CKR(pick_sub(h, &sub));
     if (sub) return pk_in_box<T>(h, sub, d, tol, max_iter, warm, so);
   }
-  const int tg = h->timing ? 1 : 0;
-  if (!pf.pk_graph[tg]) CKR(capture<T>(h, true, h->timing, &pf.pk_graph[tg]));
+  if (!pf.pk_graph[0]) CKR(capture<T>(h, true, false, &pf.pk_graph[0]));
+  if (h->timing && !pf.pk_graph[1]) CKR(capture<T>(h, true, true, &pf.pk_graph[1]));
   launch_pk_init<T>(plan_of<T>(h), h->h64, d, pf.c, pf.p, pf.t, warm ? 1 : 0, h->ew_ngrid, h->stream);
   h->launches += 1;
   CKR(init_scalars(h, tol, max_iter, 0.0));
-  CKR(run_loop(h, pf.pk_graph[tg], max_iter, true, (int)sizeof(T)));
+  CKR(run_loop(h, pf.pk_graph[0], pf.pk_graph[1], max_iter, true, (int)sizeof(T)));
   so->iterations += h->sc_host->iter;
   so->eps = h->sc_host->eps;
   if (h->sc_host->status != SC_OK) so->status = map_status(h->sc_host->status);
@@ -609,7 +615,6 @@ template <typename T>
 int run_fixed_cg(bem_ctx* h, double tol, int max_iter, double pcrit, StepOut* so) {
   CKR(ensure_fields<T>(h));
   PrecFields<T>& pf = fields_of<T>(h);
-  const int tg = h->timing ? 1 : 0;
   CKR(init_scalars(h, tol, max_iter, pcrit));
   launch_box(plan_of<T>(h), h->S, h->sc, h->stream);
   h->launches += 1;
@@ -619,7 +624,8 @@ int run_fixed_cg(bem_ctx* h, double tol, int max_iter, double pcrit, StepOut* so
     CKR(pick_sub(h, &sub));
     if (sub) return fixed_cg_in_box<T>(h, sub, tol, max_iter, pcrit, so);
   }
-  if (!pf.cg_graph[tg]) CKR(capture<T>(h, false, h->timing, &pf.cg_graph[tg]));
+  if (!pf.cg_graph[0]) CKR(capture<T>(h, false, false, &pf.cg_graph[0]));
+  if (h->timing && !pf.cg_graph[1]) CKR(capture<T>(h, false, true, &pf.cg_graph[1]));
   const size_t n = (size_t)h->nx * h->ny;
   launch_mask_field<T>(pf.p, h->S, n, h->stream);
   launch_mask_field<T>(pf.t, h->S, n, h->stream);
@@ -630,7 +636,7 @@ int run_fixed_cg(bem_ctx* h, double tol, int max_iter, double pcrit, StepOut* so
   launch_pass_c<T>(a, C_CG_G, h->stream);
   h->launches += 5;
   CKR(read_scalars(h));
-  if (!h->sc_host->done) CKR(run_loop(h, pf.cg_graph[tg], max_iter, false, (int)sizeof(T)));
+  if (!h->sc_host->done) CKR(run_loop(h, pf.cg_graph[0], pf.cg_graph[1], max_iter, false, (int)sizeof(T)));
   so->iterations += h->sc_host->iter;
   so->eps = h->sc_host->eps;
   if (h->sc_host->status != SC_OK) so->status = map_status(h->sc_host->status);
