@@ -127,6 +127,23 @@ int bem_sweep(bem_handle h, const double *profile, const double *d_steps, int ns
               double dgamma, const bem_opts *opts, bem_result *per_step, double *final_pressure);
 
 /* ---------------------------------------------------------------------------
+ * Checkpoint and resume of a sweep.  The state a sweep ends in is the pressure
+ * it returns in final_pressure and, for an adhesive sweep (Sec. 3.1), the held
+ * contact set.  bem_contact_set copies that set (Nx*Ny bytes, 1 = held, host or
+ * device memory) after bem_sweep / bem_sweep_from / bem_solve.
+ * bem_sweep_from continues a sweep from such a state: the same arguments as
+ * bem_sweep plus p_state (Nx*Ny FP64, required) and S_state (required when
+ * dgamma > 0, ignored otherwise).  An adhesive resume starts directly with the
+ * held-set step at d_steps[0] (no preload); a non-adhesive one warm-starts from
+ * p_state as the interrupted sweep would have.  With the same precision, a sweep
+ * split into two calls at any step gives the results of the single call,
+ * bitwise.  Returns as bem_sweep; BEM_EINVAL if a required state is NULL. */
+int bem_sweep_from(bem_handle h, const double *profile, const double *d_steps, int nsteps, double dgamma,
+                   const bem_opts *opts, const double *p_state, const unsigned char *S_state,
+                   bem_result *per_step, double *final_pressure);
+int bem_contact_set(bem_handle h, unsigned char *S_out);
+
+/* ---------------------------------------------------------------------------
  * Request server: many independent solves in flight on the current device.
  *
  * bem_server_create starts nworkers host threads; each runs one job at a time

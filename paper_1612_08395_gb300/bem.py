@@ -98,6 +98,9 @@ def load_library(path: str = LIB_PATH):
                               ctypes.POINTER(Opts), vp, ctypes.POINTER(Result)]
     lib.bem_sweep.argtypes = [vp, vp, vp, ip, ctypes.c_double, ctypes.POINTER(Opts),
                               ctypes.POINTER(Result), vp]
+    lib.bem_sweep_from.argtypes = [vp, vp, vp, ip, ctypes.c_double, ctypes.POINTER(Opts), vp, vp,
+                                   ctypes.POINTER(Result), vp]
+    lib.bem_contact_set.argtypes = [vp, vp]
     lib.bem_influence_table.argtypes = [vp, vp]
     lib.bem_spectrum.argtypes = [vp, vp]
     lib.bem_convolve.argtypes = [vp, ip, vp, vp]
@@ -264,6 +267,31 @@ class Handle:
         if check:
             _check(rc, allow=(BEM_ENOCONV,))
         return res, rc
+
+    def contact_set(self) -> np.ndarray:
+        """The held contact set after the last sweep or solve (uint8, Ny x Nx)."""
+        out = np.empty((self.ny, self.nx), dtype=np.uint8)
+        _check(load_library().bem_contact_set(self._h, ctypes.c_void_p(out.ctypes.data)))
+        return out
+
+    def sweep_from(self, profile, d_steps, p_state, S_state=None, dgamma=0.0, final_pressure=None,
+                   check=True, **opts):
+        """Continue a sweep from a saved state (pressure, and contact set if adhesive)."""
+        ds = np.ascontiguousarray(np.asarray(d_steps, dtype=np.float64))
+        res = (Result * len(ds))()
+        o = make_opts(**opts)
+        fp = _ptr(final_pressure, self.n, writable=True) if final_pressure is not None else None
+        sp = None
+        if S_state is not None:
+            S_state = np.ascontiguousarray(S_state, dtype=np.uint8)
+            if S_state.size != self.n:
+                raise ValueError(f"expected {self.n} elements, got {S_state.size}")
+            sp = ctypes.c_void_p(S_state.ctypes.data)
+        rc = load_library().bem_sweep_from(self._h, _ptr(profile, self.n), _ptr(ds), len(ds), dgamma,
+                                           ctypes.byref(o), _ptr(p_state, self.n), sp, res, fp)
+        if check:
+            _check(rc, allow=(BEM_ENOCONV,))
+        return list(res), rc
 
     def sweep(self, profile, d_steps, dgamma=0.0, final_pressure=None, check=True, **opts):
         ds = np.ascontiguousarray(np.asarray(d_steps, dtype=np.float64))

@@ -1259,7 +1259,8 @@ int step_adhesive_t(bem_ctx* h, const SolveCfg& cfg, double d, double pcrit, bem
 }
 
 int run_sweep(bem_ctx* h, const double* profile, const double* d_steps, int nsteps, double dgamma,
-              const bem_opts* opts, bem_result* per_step, double* final_pressure) {
+              const bem_opts* opts, bem_result* per_step, double* final_pressure,
+              const double* p_state = nullptr, const uint8_t* S_state = nullptr) {
   g_err.clear();
   if (!h) return fail(BEM_EINVAL, "NULL handle");
   CKR(validate_ptr(profile, "profile"));
@@ -1290,10 +1291,33 @@ int run_sweep(bem_ctx* h, const double* profile, const double* d_steps, int nste
   }
   CKR(upload(h, h->h64, profile, n));
   int first_bad = BEM_OK;
-  bool warm = false;  // every sweep starts from the initial guess
+  bool warm = false;  // a sweep starts from the initial guess, unless it resumes a state
+  const bool resume = p_state != nullptr;
+  if (resume) {
+    // the state a previous sweep ended in: the pressure it returned (and, when
+    // adhesive, its held contact set), in the form the next step starts from
+    if (adhesive && !S_state) return fail(BEM_EINVAL, "resuming an adhesive sweep needs the contact set");
+    CKR(upload(h, h->io64, p_state, n));
+    if (cfg.precision == BEM_PREC_FP64) {
+      CKR(ensure_fields<double>(h));
+      CK(cudaMemcpyAsync(h->f64.p, h->io64, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    } else {
+      CKR(ensure_fields<float>(h));
+      launch_to_f32(h->io64, h->f32.p, n, h->stream);
+      h->launches += 1;
+    }
+    if (adhesive) {
+      CK(cudaMemcpyAsync(h->S, S_state, n, is_device_ptr(S_state) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                         h->stream));
+    } else {
+      bem_result st{};
+      CKR(collect<double>(h, h->io64, h->io64, 0, &st));
+      warm = st.force > 0;  // as after the step that produced the state
+    }
+  }
   for (int i = 0; i < nsteps; ++i) {
     bem_result r{};
-    if (!adhesive || i == 0) {
+    if (!adhesive || (i == 0 && !resume)) {
       CKR(step_nonadhesive(h, cfg, d_steps[i], warm, &r));
       warm = r.force > 0;
       if (adhesive) {
@@ -1328,6 +1352,24 @@ extern "C" int bem_sweep(bem_handle h, const double* profile, const double* d_st
                          double dgamma, const bem_opts* opts, bem_result* per_step,
                          double* final_pressure) {
   return run_sweep(h, profile, d_steps, nsteps, dgamma, opts, per_step, final_pressure);
+}
+
+extern "C" int bem_sweep_from(bem_handle h, const double* profile, const double* d_steps, int nsteps,
+                              double dgamma, const bem_opts* opts, const double* p_state,
+                              const unsigned char* S_state, bem_result* per_step, double* final_pressure) {
+  g_err.clear();
+  if (!p_state) return fail(BEM_EINVAL, "p_state must not be NULL");
+  return run_sweep(h, profile, d_steps, nsteps, dgamma, opts, per_step, final_pressure, p_state, S_state);
+}
+
+extern "C" int bem_contact_set(bem_handle h, unsigned char* S_out) {
+  g_err.clear();
+  if (!h || !S_out) return fail(BEM_EINVAL, "NULL argument");
+  const size_t n = (size_t)h->nx * h->ny;
+  CK(cudaMemcpyAsync(S_out, h->S, n, is_device_ptr(S_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return BEM_OK;
 }
 
 extern "C" int bem_solve(bem_handle h, const double* profile, double d, double dgamma,
