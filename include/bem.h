@@ -36,6 +36,7 @@ extern "C" {
 #define BEM_ENUMERIC (-4) /* NaN/Inf met in a reduction                         */
 #define BEM_ETIMEOUT (-5) /* a bounded device-side wait gave up                 */
 #define BEM_ECUDA (-6)    /* a CUDA runtime call failed                         */
+#define BEM_ECANCELED (-7) /* a server job was cancelled before it started       */
 
 /* Arithmetic of the transform and the fields.  BEM_PREC_FP64: everything in
  * FP64 (the plain path).  BEM_PREC_FP32: FFT passes and fields in FP32, CG
@@ -164,6 +165,10 @@ int bem_contact_set(bem_handle h, unsigned char *S_out);
  *   exceeds the budget.
  * bem_server_poll: moves up to max completion records into out, waiting up to
  *   wait_ms for the first; returns how many.  Times are seconds since create.
+ * bem_server_cancel: removes the job with this tag if it is still queued (not
+ *   started); its completion record then carries BEM_ECANCELED.  Returns BEM_OK
+ *   when cancelled, BEM_EINVAL when no queued job has the tag (already running,
+ *   finished or unknown).
  * bem_server_pending: jobs queued or running.
  * bem_server_bytes: device bytes accounted to cached and running handles.
  * bem_server_footprint: the bytes admission reserves for a job on an Nx x Ny
@@ -194,6 +199,7 @@ typedef struct bem_server *bem_server_handle;
 int bem_server_create(int nworkers, size_t hbm_budget_bytes, bem_server_handle *out);
 int bem_server_submit(bem_server_handle s, const bem_job *job);
 int bem_server_poll(bem_server_handle s, bem_completion *out, int max, int wait_ms);
+int bem_server_cancel(bem_server_handle s, long long tag);
 int bem_server_pending(bem_server_handle s);
 size_t bem_server_bytes(bem_server_handle s);
 size_t bem_server_footprint(int Nx, int Ny);

@@ -22,6 +22,7 @@ BEM_ENOCONV = -3
 BEM_ENUMERIC = -4
 BEM_ETIMEOUT = -5
 BEM_ECUDA = -6
+BEM_ECANCELED = -7
 PREC_FP64 = 0
 PREC_FP32 = 1
 PREC_FP32_REFINE = 2
@@ -119,6 +120,7 @@ def load_library(path: str = LIB_PATH):
     lib.bem_server_submit.argtypes = [vp, ctypes.POINTER(Job)]
     lib.bem_server_poll.argtypes = [vp, ctypes.POINTER(Completion), ip, ip]
     lib.bem_server_pending.argtypes = [vp]
+    lib.bem_server_cancel.argtypes = [vp, ctypes.c_longlong]
     lib.bem_server_bytes.argtypes = [vp]
     lib.bem_server_bytes.restype = ctypes.c_size_t
     lib.bem_server_footprint.argtypes = [ip, ip]
@@ -346,6 +348,10 @@ class Server:
             out.append({"tag": c.tag, "status": c.status, "t_submit": c.t_submit, "t_start": c.t_start,
                         "t_end": c.t_end, "results": list(res), "final_pressure": fp})
         return out
+
+    def cancel(self, tag):
+        """Cancel a job that has not started; True when it was still queued."""
+        return load_library().bem_server_cancel(self._s, tag) == BEM_OK
 
     def pending(self):
         return load_library().bem_server_pending(self._s)

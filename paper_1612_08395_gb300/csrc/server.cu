@@ -269,6 +269,26 @@ extern "C" int bem_server_poll(bem_server_handle s, bem_completion* out, int max
   return n;
 }
 
+extern "C" int bem_server_cancel(bem_server_handle s, long long tag) {
+  if (!s) return bem::set_error(BEM_EINVAL, "bem_server_cancel: NULL server");
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
+      if (it->job.tag != tag) continue;
+      bem_completion c{};
+      c.tag = tag;
+      c.status = BEM_ECANCELED;
+      c.t_submit = it->t_submit;
+      c.t_start = c.t_end = now_s(s->t0);
+      s->queue.erase(it);
+      s->done.push_back(c);
+      s->cv_done.notify_all();
+      return BEM_OK;
+    }
+  }
+  return bem::set_error(BEM_EINVAL, "bem_server_cancel: no queued job with this tag");
+}
+
 extern "C" int bem_server_pending(bem_server_handle s) {
   if (!s) return BEM_EINVAL;
   std::lock_guard<std::mutex> lk(s->mu);

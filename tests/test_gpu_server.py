@@ -135,3 +135,22 @@ def test_batch_fp32_refine_matches_fp64(bem_mod):
         if nrm > 0:
             assert np.linalg.norm(pa - pb) <= 1e-5 * nrm
         assert ca["results"][-1].contact_count == cb["results"][-1].contact_count
+
+
+def test_cancel_a_queued_job(bem_mod):
+    """One worker busy with a 1024^2 adhesive sweep: the job queued behind it can
+    be cancelled (its completion carries BEM_ECANCELED, its arrays are untouched);
+    the running job cannot, and finishes normally."""
+    n = 1024
+    h = I.paraboloid(n)
+    steps = np.linspace(0.02, -0.02, 81)
+    with bem_mod.Server(nworkers=1, hbm_budget_bytes=8 << 30) as srv:
+        t_run = srv.submit(n, n, 1.0 / n, 1.0 / n, 0.3, 0.3, h, steps, dgamma=1e-3, precision="fp32")
+        p = np.full((64, 64), -7.0)
+        t_q = srv.submit(64, 64, 1 / 64, 1 / 64, 0.3, 0.3, I.paraboloid(64), [0.01], final_pressure=p)
+        assert srv.cancel(t_q)
+        assert not srv.cancel(t_q)  # no longer queued
+        comps = {c["tag"]: c for c in srv.drain()}
+    assert comps[t_q]["status"] == bem_mod.BEM_ECANCELED
+    assert (p == -7.0).all()
+    assert comps[t_run]["status"] == bem_mod.BEM_OK
