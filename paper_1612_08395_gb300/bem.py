@@ -13,7 +13,9 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "_build", "libbem_gb300.so")
+# BEM_DEBUG_CHECKS=1 selects the bounds-checked debug build (build.py)
+LIB_PATH = os.path.join(_PKG, "_build_debug" if os.environ.get("BEM_DEBUG_CHECKS", "0") == "1" else "_build",
+                        "libbem_gb300.so")
 
 BEM_OK = 0
 BEM_EINVAL = -1

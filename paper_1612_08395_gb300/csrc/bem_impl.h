@@ -54,7 +54,8 @@ struct Scalars {
   int band0, band1, col0, col1;
   unsigned int cnt_a, cnt_c, cnt_e, cnt_r;  // last-block arrival counters
   // Sticky device error bits (kept across solves: init_scalars does not copy
-  // this member); 1 = a kernel gave up waiting for its own asynchronous copies.
+  // this member); 1 = a kernel gave up waiting for its own asynchronous copies,
+  // 2 = a bounds check of a debug build (-DBEM_DEBUG_CHECKS) failed.
   unsigned int kerr, pad2;
 };
 

@@ -299,6 +299,20 @@ __device__ __forceinline__ void block_sum(double (&v)[NQ], double* red) {
 }
 
 // ---------------------------------------------------------------------------
+// Debug builds (-DBEM_DEBUG_CHECKS): bounds checks on the index arithmetic of
+// the transposed intermediate W.  A failed check sets bit 2 of the handle's
+// sticky error word and skips the access (no trap); release builds compile the
+// checks away.
+#ifdef BEM_DEBUG_CHECKS
+__device__ __forceinline__ bool bem_check(bool ok, unsigned int* err) {
+  if (!ok && err) atomicOr(err, 2u);
+  return ok;
+}
+#else
+__device__ __forceinline__ constexpr bool bem_check(bool, unsigned int*) { return true; }
+#endif
+
+// ---------------------------------------------------------------------------
 // Bulk asynchronous copies (global -> shared, contiguous, 16-byte aligned and
 // sized) that complete on a shared-memory mbarrier.  Waits are bounded: after
 // kMbarTries unsuccessful polls the caller gets `false` and gives up.

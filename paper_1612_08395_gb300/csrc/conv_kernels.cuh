@@ -263,9 +263,11 @@ __device__ __forceinline__ void split_two(const C<T>* s, int pk, int pm, C<T> w,
 }
 template <typename T, int M>
 __device__ __forceinline__ void split_store(const C<T>* sm, int rs, int nb, int lognb, int row0, int nrows,
-                                            const int* sp, const C<T>* tws, C<T>* W, int rows_w) {
+                                            const int* sp, const C<T>* tws, C<T>* W, int rows_w,
+                                            unsigned int* kerr) {
   constexpr int hm = M / 2 + 1;
   const int rows = min(nb, nrows - row0);
+  const size_t wlim = (size_t)(M + 1) * rows_w;  // W holds (M+1) rows of rows_w
   if (sizeof(T) == 4 && nb >= 2 && (rows_w & 1) == 0) {
     const int lp = lognb - 1;  // row pairs per group
     for (int idx = threadIdx.x; idx < hm << lp; idx += blockDim.x) {
@@ -293,6 +295,7 @@ __device__ __forceinline__ void split_store(const C<T>* sm, int rs, int nb, int 
       const int km = k == 0 ? M : M - k;
       C<T>* wk = W + (size_t)k * rows_w + row0 + b0;
       C<T>* wm = W + (size_t)km * rows_w + row0 + b0;
+      if (!bem_check((size_t)km * rows_w + row0 + b0 + (two ? 1 : 0) < wlim && row0 + b0 < rows_w, kerr)) continue;
       if (two) {
         *reinterpret_cast<float4*>(wk) = make_float4((float)xk0.x, (float)xk0.y, (float)xk1.x, (float)xk1.y);
         if (km != k) *reinterpret_cast<float4*>(wm) = make_float4((float)xm0.x, (float)xm0.y, (float)xm1.x, (float)xm1.y);
@@ -316,6 +319,7 @@ __device__ __forceinline__ void split_store(const C<T>* sm, int rs, int nb, int 
       split_two<T>(s, __ldg(sp + k), __ldg(sp + M - k), __ldg(tws + k), xk, xm);
     }
     const int km = k == 0 ? M : M - k;
+    if (!bem_check((size_t)km * rows_w + row0 + bb < wlim && row0 + bb < rows_w, kerr)) continue;
     W[(size_t)k * rows_w + row0 + bb] = xk;
     if (km != k) W[(size_t)km * rows_w + row0 + bb] = xm;
   }
@@ -345,7 +349,7 @@ __global__ void BEM_ROW_BOUNDS(LOGL) k_pass_a(PassArgs<T> a) {
     if (sc->done) return;
   }
   const int nb = a.pl.nbA, lognb = a.pl.lognbA, rs = a.pl.gA.rs;
-  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int tid = threadIdx.x;
   const int b = tid >> (LOGL - 3), t = tid & (L8 - 1);
   const int row0 = blockIdx.x * nb;
   const int row = row0 + b;
@@ -421,7 +425,7 @@ __global__ void BEM_ROW_BOUNDS(LOGL) k_pass_a(PassArgs<T> a) {
   }
   // split the packed transform into the half spectrum, store transposed
   split_store<T, M>(sm, rs, nb, lognb, row0, nrows, a.spA, reinterpret_cast<const Cx*>(a.twS),
-                    reinterpret_cast<Cx*>(a.W), a.rows_w);
+                    reinterpret_cast<Cx*>(a.W), a.rows_w, a.kerr);
 }
 
 // ---------------------------------------------------------------------------
@@ -511,7 +515,7 @@ __global__ void BEM_ROWP_BOUNDS(LOGL) k_pass_ap(PassArgs<T> a) {
     if (sc->done) return;
   }
   const int nb = a.pl.nbA, lognb = a.pl.lognbA, rs = a.pl.gA.rs;
-  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int tid = threadIdx.x;
   const int b = tid >> (LOGL - 3), t = tid & (L8 - 1);
   const int ncols = a.ncols_in, nrows = a.nrows_in;
   const int half = (ncols + 1) >> 1;
@@ -591,7 +595,7 @@ __global__ void BEM_ROWP_BOUNDS(LOGL) k_pass_ap(PassArgs<T> a) {
       F::dif(buf, t, ls, tw);
       __syncthreads();
     }
-    split_store<T, M>(sm, rs, nb, lognb, row0, nrows, sp, tws, W, a.rows_w);
+    split_store<T, M>(sm, rs, nb, lognb, row0, nrows, sp, tws, W, a.rows_w, a.kerr);
   }
   if (MODE == A_PK_P) {
     double vv[3] = {(double)acc[0], (double)acc[1], (double)acc[2]};
@@ -643,7 +647,7 @@ __global__ void __launch_bounds__((LOGL) >= 13 ? 1024 : 512, (LOGL) >= 13 ? 1 : 
     v[e] = mk<T>(0, 0);
     if (HALF && !F::first_half(e)) continue;
     const int y = F::n0(t, e);
-    if (act && y >= ylo && y <= yhi) v[e] = W[coff + y];
+    if (act && y >= ylo && y <= yhi && bem_check(coff + y < (size_t)(M + 1) * rin, a.kerr)) v[e] = W[coff + y];
   }
   F::stage0_fwd(v, t, tw);
 #pragma unroll
@@ -701,7 +705,7 @@ __global__ void __launch_bounds__((LOGL) >= 13 ? 1024 : 512, (LOGL) >= 13 ? 1 : 
     for (int e = 0; e < 8; ++e) {
       if (!F::first_half(e)) continue;
       const int y = F::n0(t, e);
-      if (y >= ylo && y <= yhi) W[coff + y] = v[e];
+      if (y >= ylo && y <= yhi && bem_check(coff + y < (size_t)(M + 1) * rin, a.kerr)) W[coff + y] = v[e];
     }
   }
   (void)R0;
@@ -970,8 +974,10 @@ __global__ void BEM_ROW_BOUNDS(LOGL) k_pass_c(PassArgs<T> a) {
       if (idx < total) {
         const int k = idx >> lognb, rw = row0 + (idx & (nb - 1));
         if (rw < ny) {
-          xk[j] = W[(size_t)k * a.rows_w + rw];
-          xm[j] = W[(size_t)(M - k) * a.rows_w + rw];
+          if (bem_check(k <= M && rw < a.rows_w, a.kerr)) {
+            xk[j] = W[(size_t)k * a.rows_w + rw];
+            xm[j] = W[(size_t)(M - k) * a.rows_w + rw];
+          }
         }
       }
     }
@@ -1104,12 +1110,14 @@ __global__ void BEM_ROWP_BOUNDS(LOGL) k_pass_cp(PassArgs<T> a) {
       const int lh = lognb - 1;
       for (int q = tid; q < (M + 1) << lh; q += nthr) {
         const int k = q >> lh, j = q & ((1 << lh) - 1);
-        cp_async16(wst + (k << lognb) + 2 * j, W + (size_t)k * a.rows_w + r0 + 2 * j);
+        if (bem_check(r0 + 2 * j + 1 < a.rows_w, a.kerr))
+          cp_async16(wst + (k << lognb) + 2 * j, W + (size_t)k * a.rows_w + r0 + 2 * j);
       }
     } else {
       for (int q = tid; q < (M + 1) << lognb; q += nthr) {
         const int k = q >> lognb, bb = q & (nb - 1);
-        if (bb < rows) cp_async_cx<Cx>(wst + q, W + (size_t)k * a.rows_w + r0 + bb);
+        if (bb < rows && bem_check(r0 + bb < a.rows_w, a.kerr))
+          cp_async_cx<Cx>(wst + q, W + (size_t)k * a.rows_w + r0 + bb);
       }
     }
     cp_async_commit();

@@ -297,8 +297,9 @@ int download(bem_ctx* h, double* dst, const double* src, size_t n) {
 }
 
 int device_error(bem_ctx* h) {
-  return fail(BEM_ETIMEOUT, "a kernel gave up waiting for its own asynchronous copies (error bits %#x)",
-              h->sc_host->kerr);
+  const unsigned e = h->sc_host->kerr;
+  if (e & 2u) return fail(BEM_ECUDA, "a debug bounds check failed in a kernel (error bits %#x)", e);
+  return fail(BEM_ETIMEOUT, "a kernel gave up waiting for its own asynchronous copies (error bits %#x)", e);
 }
 
 int read_scalars(bem_ctx* h) {

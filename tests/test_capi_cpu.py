@@ -105,3 +105,18 @@ def test_library_resolves_all_symbols_at_load(bem_mod):
     binding (an uninstantiated template would fail here, not at first call)."""
     import ctypes
     ctypes.CDLL(bem_mod.LIB_PATH, mode=os.RTLD_NOW)
+
+
+def test_debug_checks_compile():
+    """The bounds-checked kernels (-DBEM_DEBUG_CHECKS) compile; the debug build
+    goes to its own directory, so it never replaces the release library."""
+    import subprocess
+    import tempfile
+    from paper_1612_08395_gb300 import build as B
+    assert B.DEBUG_LIB != B.LIB and os.path.dirname(B.DEBUG_LIB) != os.path.dirname(B.LIB)
+    with tempfile.TemporaryDirectory() as d:
+        for src in ("kern_f32_b.cu", "kern_f64_b.cu"):
+            cmd = [B.nvcc(), *B.ARCH, *B.FLAGS, "-DBEM_DEBUG_CHECKS", "-c", os.path.join(B.CSRC, src),
+                   "-o", os.path.join(d, src + ".o")]
+            r = subprocess.run(cmd, capture_output=True, text=True)
+            assert r.returncode == 0, r.stderr[-2000:]
