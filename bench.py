@@ -28,6 +28,9 @@ batch       : (rank 0, one GPU) the seeded batch mix of independent solves
               the largest final-pressure difference between the two
 serving     : the Poisson request stream (200/s) through the server and through
               the plain FP64 path: solves/s and p50/p99 latency from arrival
+rough_4096  : (rank 0) the 4096^2 non-adhesive rough-surface solve on the 8192^2
+              torus in each precision: CG iterations/s, contact fraction, force,
+              and the passes' durations and bandwidth
 
 --impl reference times the oracle alone (rank 0) and prints its own line.
 """
@@ -281,6 +284,49 @@ def batch_and_serving(bem, inputs, n_batch, n_serve, workers):
     return out
 
 
+def rough_4096(bem, inputs, torch, precisions=("fp32", "fp32_refine", "fp64")):
+    """The 4096^2 non-adhesive workload: one solve of the seeded self-affine
+    surface (H = 0.8, q1/q0 = 256, rms slope 0.1, PCG64 seed 1612) at d = rms
+    height, k = 0.3, nu = 0.3, on the 8192^2 torus, per precision: CG iterations/s
+    over the whole solve (CUDA events; the first solve of each precision is a
+    warm-up), contact fraction and force, and the passes' average durations and
+    bandwidth from the live pass timing."""
+    n = 4096
+    dx = 1.0 / n
+    hgt, zrms = inputs.rough_self_affine(n, hurst=0.8, q1_over_q0=256.0, rms_slope=0.1, seed=1612)
+    h_dev = torch.from_numpy(hgt).cuda()
+    p_dev = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    hbm, _ = peaks()
+    out = {"workload": "non-adhesive self-affine rough surface 4096x4096 (H=0.8, q1/q0=256, rms slope 0.1, "
+                       "seed 1612), d = rms height, k=0.3, nu=0.3, 8192^2 torus"}
+    with bem.Handle(n, n, dx, dx, K_EXP, NU, E0, C0) as hd:
+        for prec in precisions:
+            hd.solve(h_dev, zrms, pressure_out=p_dev, precision=prec, stream=stream)
+            torch.cuda.synchronize()
+            hd.pass_times(reset=True)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res, rc = hd.solve(h_dev, zrms, pressure_out=p_dev, precision=prec, stream=stream,
+                               time_passes=prec != "fp32_refine")
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            entry = {"iterations": res.iterations, "ms": ms, "iter_per_s": 1e3 * res.iterations / ms,
+                     "contact_fraction": res.contact_count / (n * n), "force": res.force, "status": rc}
+            if prec != "fp32_refine":
+                wb, _ = hd.pass_work()
+                pms, pn, _ = hd.pass_times(reset=True)
+                if pn:
+                    avg = [m / pn for m in pms]
+                    entry["pass_us"] = {k: 1e3 * v for k, v in zip("ABC", avg)}
+                    entry["pass_gbs"] = {k: b / (v * 1e-3) / 1e9 for k, b, v in zip("ABC", wb, avg)}
+                    entry["pass_hbm_frac"] = {k: g / hbm for k, g in entry["pass_gbs"].items()}
+            out[prec] = entry
+    return {"rough_4096": out}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -297,6 +343,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=32,
                     help="requests of the Poisson stream to serve (0 = skip)")
     ap.add_argument("--workers", type=int, default=8, help="server worker streams")
+    ap.add_argument("--no-rough-4096", action="store_true",
+                    help="skip the 4096^2 rough-surface solves reported after the timed region")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -454,6 +502,8 @@ def main():
                                           "(oracle FFT mode, numpy pocketfft FP64, single thread)"}
     h.close()
     del l2_flush
+    if rank == 0 and world == 1 and not args.no_rough_4096:
+        line.update(rough_4096(bem, inputs, torch))
     if rank == 0 and world == 1 and (args.batch_jobs or args.serve_requests):
         line.update(batch_and_serving(bem, inputs, args.batch_jobs, args.serve_requests, args.workers))
     if rank == 0:
