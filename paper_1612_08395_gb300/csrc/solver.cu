@@ -511,7 +511,13 @@ int pick_sub(bem_ctx* h, bem_ctx** out) {
   for (bem_ctx* c : h->subs)
     if (c->px == qx && c->py == qy) { *out = c; return BEM_OK; }
   bem_ctx* c = nullptr;
-  if (create_ctx(qx / 2, qy / 2, h->dx, h->dy, h->k, h->nu, h->E0, h->c0, h, &c) != BEM_OK) {
+  // BEM_INJECT_SUB_FAILURE=1 makes every sub-context creation fail as an
+  // allocation failure would (host-side fault injection for the fallback below)
+  const char* inj = getenv("BEM_INJECT_SUB_FAILURE");
+  const int rc = inj && inj[0] == '1'
+                     ? fail(BEM_ENOMEM, "sub-context allocation failed (injected)")
+                     : create_ctx(qx / 2, qy / 2, h->dx, h->dy, h->k, h->nu, h->E0, h->c0, h, &c);
+  if (rc != BEM_OK) {
     // no room for the smaller torus (or it failed to set up): the whole grid gives
     // the same result, so carry on there
     g_err.clear();

@@ -7,6 +7,9 @@ closed_forms.jkr_force / jkr_depth).  The contact is preloaded without
 adhesion to the radius a0 and can only shrink afterwards, so the comparison is
 with the minima over a <= a0.
 
+The same closed form at 2048 x 2048 on the load-unload sweep (k = 0.3, preload
+d0 = 0.02, 400 unloading steps of 1.1e-4): force minimum and jump-off depth.
+
 Fig. 10: adhesive pull-off of a flat square punch whose edges make 0, 15, 30 and
 45 degrees with the grid (k = 0.3, 512 x 512): the macroscopic curve does not
 depend on the orientation -- pull-off force, jump-off depth and initial contact
@@ -56,6 +59,30 @@ def test_fig8_pull_off_converges_with_mesh(bem_mod, cuda_ok):
     for q in range(2):
         assert errs[0][q] > errs[1][q] > errs[2][q]
     assert errs[2][0] < 0.03 and errs[2][1] < 0.03
+
+
+def test_pull_off_2048_follows_jkr(bem_mod, cuda_ok):
+    # the 2048 x 2048 load-unload sweep (k = 0.3, preload d0 = 0.02, 400 unloading steps
+    # of 1.1e-4): the contact starts at the Hertz radius a0 and shrinks, so the force
+    # minimum is the closed form's minimum over a <= a0 (at a0 here) and the last contact
+    # depth the closed form's jump-off depth
+    from oracle import closed_forms as CF
+    n, k, nu, R, gam, d0 = 2048, 0.3, 0.3, 1.0, 1e-3, 0.02
+    a0 = CF.hertz_radius(d0, k, R)
+    aa = np.linspace(1e-3, a0, 4000)
+    Fmin = min(CF.jkr_force(x, k, nu, R, gam) for x in aa)
+    dmin = min(CF.jkr_depth(x, k, nu, R, gam) for x in aa)
+    steps = np.array([d0] + [d0 - 1.1e-4 * j for j in range(1, 401)])
+    with bem_mod.Handle(n, n, 1.0 / n, 1.0 / n, k, nu) as hd:
+        res, rc = hd.sweep(I.paraboloid(n, R), steps, dgamma=gam, precision="fp32")
+    assert rc == bem_mod.BEM_OK
+    F = np.array([r.force for r in res])
+    cnt = np.array([r.contact_count for r in res])
+    assert cnt[-1] == 0
+    # preload: graded Hertz (Eqs. 15, 16)
+    assert F[0] == pytest.approx(CF.hertz_force(a0, k, nu, R), rel=1e-3)
+    assert F.min() == pytest.approx(Fmin, rel=0.01)
+    assert steps[np.flatnonzero(cnt > 0).max()] == pytest.approx(dmin, abs=1.1e-4)
 
 
 def test_fig10_square_punch_orientation_independent(bem_mod, cuda_ok):
