@@ -5,9 +5,11 @@ baseline / reference leg of ``bench.py`` may import, call, link or run anything
 under oracle/.  The product library (paper_1612_08395_gb300) never touches it,
 and it never imports the product: the two share no code.
 
-Parity status: every function is pinned by the tests in tests/test_oracle_*.py
-except alpha(k, nu) for k != 0, which is "parity unpinned": every closed form
-the paper offers carries the same alpha, so an error in Eq. 3 would cancel.
+Parity status: every function is pinned by the tests in tests/test_oracle_*.py.
+alpha(k, nu) is pinned only at k = 0 (Boussinesq) and in the limit k -> 1 at
+nu = 0.5 (Gibson's incompressible soil, alpha / (1 - k) -> 1 / pi); between
+them it rests on Eq. 3 as printed, since every closed form the paper offers
+carries the same alpha and an error there would cancel.
 """
 from .bem_oracle import *  # noqa: F401,F403
 from . import closed_forms  # noqa: F401

@@ -103,3 +103,21 @@ def test_detach_sign_is_caught(oracle_mod):
         lost = [o["d"] for o in out if o["count"] == 0]
         caught = bool(lost) and abs(lost[0] / -dc - 1) < 0.1
         assert caught == ok
+
+
+@pytest.mark.parametrize("old,new", [("(2.0 ** k)", "(2.0 ** (-k))"),
+                                     ("math.gamma(1.0 + k / 2.0)", "math.gamma(1.0 + k)"),
+                                     ("math.gamma((3.0 + k - b) / 2.0)", "math.gamma((3.0 - k - b) / 2.0)")])
+def test_alpha_mistakes_invisible_at_k0_are_caught(oracle_mod, old, new):
+    # each mistake leaves alpha(0, nu) = 1/pi (the Boussinesq pin passes) but
+    # breaks Gibson's limit alpha(k, 0.5) / (1 - k) -> 1/pi as k -> 1
+    import math
+    bad = _mutant(oracle_mod.alpha, old, new)
+    k = 0.999
+
+    def gibson_gap(f):
+        return abs(math.pi * f(k, 0.5) / (1.0 - k) - 1.0)
+
+    assert bad(0.0, 0.3) == pytest.approx(1.0 / math.pi, rel=1e-15)
+    assert gibson_gap(oracle_mod.alpha) <= 1.0 - k
+    assert gibson_gap(bad) > 10 * (1.0 - k)  # the pin (gap <= 1 - k) fails by a margin

@@ -24,6 +24,17 @@ def test_alpha_homogeneous_is_boussinesq(oracle_mod, nu):
     assert oracle_mod.beta(0.0, nu) == pytest.approx(1.0, rel=1e-15)
 
 
+@pytest.mark.parametrize("k", [0.99, 0.999, 0.9999])
+def test_alpha_gibson_limit(oracle_mod, k):
+    # k -> 1 at nu = 0.5 is Gibson's incompressible soil (shear modulus m z, so
+    # E0 / c0 = 3 m): its surface responds locally, w = p / (2 m) (Gibson 1967).
+    # The kernel (1 - k) / (2 pi r^(1+k)) tends to the 2D delta, so Eq. 2 gives
+    # w -> alpha (1 - nu^2) c0 p 2 pi / ((1 - k) E0) and alpha / (1 - k) -> 1 / pi,
+    # independently of Eq. 3; the approach is linear in 1 - k.
+    ratio = math.pi * oracle_mod.alpha(k, 0.5) / (1.0 - k)
+    assert abs(ratio - 1.0) <= 1.0 - k
+
+
 def test_beta_definition(oracle_mod):
     # Eq. 4 at nu = 0 is sqrt(1+k); at nu = 0.5 it is sqrt((1+k)(1-k)).
     for k in (-0.7, -0.2, 0.4, 0.9):
