@@ -37,12 +37,17 @@ def test_alpha_matches_oracle(bem_mod, oracle_mod, k, nu):
 
 
 def test_alpha_limits(bem_mod):
-    # Boussinesq at k = 0 (any nu) and Gibson's incompressible soil as k -> 1 at
-    # nu = 0.5, where alpha / (1 - k) -> 1 / pi (a local, Winkler-type response)
+    # Boussinesq at k = 0 (any nu), Gibson's incompressible soil as k -> 1 at
+    # nu = 0.5, where alpha / (1 - k) -> 1 / pi (a local, Winkler-type response),
+    # and the purely radial stress field at nu = 1/(2+k)
     for nu in (0.0, 0.3, 0.5):
         assert bem_mod.alpha(0.0, nu) == pytest.approx(1.0 / math.pi, rel=1e-14)
     for k in (0.999, 0.9999):
         assert abs(math.pi * bem_mod.alpha(k, 0.5) / (1.0 - k) - 1.0) <= 1.0 - k
+    # Frohlich-Holl radial-stress field at nu = 1/(2+k)
+    for k in (0.1, 0.4, 0.8):
+        assert bem_mod.alpha(k, 1.0 / (2.0 + k)) == pytest.approx(
+            (2.0 + k) / (2.0 * math.pi * (1.0 + k) ** 2), rel=1e-13)
 
 
 def test_alpha_invalid_is_nan(bem_mod):

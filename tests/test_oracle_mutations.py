@@ -121,3 +121,18 @@ def test_alpha_mistakes_invisible_at_k0_are_caught(oracle_mod, old, new):
     assert bad(0.0, 0.3) == pytest.approx(1.0 / math.pi, rel=1e-15)
     assert gibson_gap(oracle_mod.alpha) <= 1.0 - k
     assert gibson_gap(bad) > 10 * (1.0 - k)  # the pin (gap <= 1 - k) fails by a margin
+
+
+def test_alpha_mistakes_split_between_the_two_pins(oracle_mod):
+    # a dropped beta factor is invisible where beta = 1 (the Frohlich-Holl line)
+    # but breaks Gibson's limit (beta -> 0); a wrong Gamma(2+k) keeps the
+    # Boussinesq value at k = 0 and leaves the Frohlich-Holl line
+    import math
+    k = 0.999
+    fh = lambda f, kk: f(kk, 1.0 / (2.0 + kk)) / ((2.0 + kk) / (2.0 * math.pi * (1.0 + kk) ** 2)) - 1.0
+    no_beta = _mutant(oracle_mod.alpha, "(2.0 ** k) * b * math.sin", "(2.0 ** k) * math.sin")
+    assert abs(fh(no_beta, 0.5)) < 1e-13
+    assert abs(math.pi * no_beta(k, 0.5) / (1.0 - k) - 1.0) > 10 * (1.0 - k)
+    bad_gamma = _mutant(oracle_mod.alpha, "math.gamma(2.0 + k)", "math.gamma(1.0 + k)")
+    assert bad_gamma(0.0, 0.3) == pytest.approx(1.0 / math.pi, rel=1e-15)
+    assert abs(fh(bad_gamma, 0.5)) > 0.1

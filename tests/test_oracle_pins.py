@@ -35,6 +35,21 @@ def test_alpha_gibson_limit(oracle_mod, k):
     assert abs(ratio - 1.0) <= 1.0 - k
 
 
+@pytest.mark.parametrize("k", [0.05, 0.2, 0.3, 0.5, 0.7, 0.9])
+def test_alpha_frohlich_holl(oracle_mod, k):
+    # nu = 1/(2+k) (beta = 1): the point-load field of E = E0 (z/c0)^k is purely
+    # radial, sigma_R = n F cos^(n-2)(theta) / (2 pi R^2) with n = 3 + k (it carries F
+    # and satisfies equilibrium).  Integrating its strains sigma_R/E and -nu sigma_R/E
+    # in spherical coordinates gives u_R ~ cos(theta) / R^(1+k) and u_theta ~
+    # sin(theta) / R^(1+k) with zero shear strain, and at the surface
+    # |u_z| = n F c0^k / (2 pi (1+k) (2+k) E0 r^(1+k)).  Matching Eq. 2 with
+    # 1 - nu^2 = (1+k)(3+k)/(2+k)^2 gives alpha = (2+k) / (2 pi (1+k)^2).
+    nu = 1.0 / (2.0 + k)
+    assert oracle_mod.beta(k, nu) == pytest.approx(1.0, rel=1e-14)
+    assert oracle_mod.alpha(k, nu) == pytest.approx((2.0 + k) / (2.0 * math.pi * (1.0 + k) ** 2),
+                                                     rel=1e-13)
+
+
 def test_beta_definition(oracle_mod):
     # Eq. 4 at nu = 0 is sqrt(1+k); at nu = 0.5 it is sqrt((1+k)(1-k)).
     for k in (-0.7, -0.2, 0.4, 0.9):
