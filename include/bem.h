@@ -35,7 +35,8 @@ extern "C" {
 #define BEM_ENOCONV (-3)  /* CG hit max_iter; results are the last iterate      */
 #define BEM_ENUMERIC (-4) /* NaN/Inf met in a reduction                         */
 #define BEM_ETIMEOUT (-5) /* a bounded device-side wait gave up                 */
-#define BEM_ECUDA (-6)    /* a CUDA runtime call failed                         */
+#define BEM_ECUDA (-6)    /* a CUDA runtime call failed, or (debug builds with
+                             BEM_DEBUG_CHECKS) a kernel's bounds check failed  */
 #define BEM_ECANCELED (-7) /* a server job was cancelled before it started       */
 
 /* Arithmetic of the transform and the fields.  BEM_PREC_FP64: everything in
