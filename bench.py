@@ -164,10 +164,13 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (host)"},
+            "data": "synthetic", "config": {"workload": WORKLOAD, "precision": "fp64 (oracle)",
+                                            "grid": [N, N], "torus": [2 * N, 2 * N],
+                                            "parallelism": "rank 0 only", "l2": "n/a (host)"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "2 Polonsky-Keer CG iterations of the 2048^2 preload per step "
-                                       "(oracle FFT mode, numpy pocketfft FP64, single thread)"},
+                                       "(oracle FFT mode, numpy pocketfft FP64, single thread)",
+                             "host": host_cpu()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -189,6 +192,24 @@ def cpu_oracle_sample_cached(iters):
     t0 = time.perf_counter()
     res = oracle.pk_solve(A, conv, h, D0, tol=1e-300, max_iter=iters)
     return res.iterations, time.perf_counter() - t0, 0.0
+
+
+def host_cpu():
+    """nproc and the CPU model of this host, for the oracle's timing."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    return {"nproc": os.cpu_count(), "cpu": model}
 
 
 def _pct(v, q):
@@ -499,7 +520,8 @@ def main():
         it, el, _ = cpu_oracle_sample_cached(3)
         line["cpu_baseline"] = {"value": it / el, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": "3 Polonsky-Keer CG iterations of the 2048^2 preload solve "
-                                          "(oracle FFT mode, numpy pocketfft FP64, single thread)"}
+                                          "(oracle FFT mode, numpy pocketfft FP64, single thread)",
+                                "host": host_cpu()}
     h.close()
     del l2_flush
     if rank == 0 and world == 1 and not args.no_rough_4096:
