@@ -136,3 +136,56 @@ def test_alpha_mistakes_split_between_the_two_pins(oracle_mod):
     bad_gamma = _mutant(oracle_mod.alpha, "math.gamma(2.0 + k)", "math.gamma(1.0 + k)")
     assert bad_gamma(0.0, 0.3) == pytest.approx(1.0 / math.pi, rel=1e-15)
     assert abs(fh(bad_gamma, 0.5)) > 0.1
+
+
+def test_p_crit_element_size_exponent_is_caught(oracle_mod):
+    # Eq. 24 scales with delta^-(1-k)/2; a flipped exponent breaks the energy
+    # balance U_el = dgamma delta^2 (Eqs. 21-22) behind it
+    k, nu, g, dl, c1 = 0.3, 0.3, 1e-3, 1.0 / 2048, 5.62
+    A = oracle_mod.compliance(k, nu)
+
+    def balance(f):
+        pc = f(k, nu, g, dl, c1=c1)
+        return A * pc ** 2 / 2 * dl ** (3 - k) * c1 / (g * dl * dl) - 1.0
+
+    bad = _mutant(oracle_mod.p_crit, "delta ** (1.0 - k)", "delta ** (1.0 + k)")
+    assert abs(balance(oracle_mod.p_crit)) < 1e-13
+    assert abs(balance(bad)) > 0.5
+
+
+def test_unmasked_fixed_set_transform_is_caught(oracle_mod):
+    # the fixed-set CG must restrict r = A K t to the held set; without the mask
+    # the iterate leaves the set and no longer solves the reduced system
+    n, k = 6, -0.2
+    dx = 1.0 / n
+    A = oracle_mod.compliance(k, 0.3)
+    Kq = oracle_mod.influence_quarter(k, dx, dx, n, n)
+    conv = oracle_mod.DirectConvolver(Kq, n, n)
+    rng = np.random.Generator(np.random.PCG64(5))
+    S = rng.random((n, n)) < 0.6
+    c = rng.random((n, n)) - 0.5
+    Kfull = np.array([[Kq[abs(a // n - b // n), abs(a % n - b % n)] for b in range(n * n)]
+                      for a in range(n * n)])
+    s = S.ravel()
+    ref = np.linalg.solve(A * Kfull[np.ix_(s, s)], -c.ravel()[s])
+    bad = _mutant(oracle_mod.fixed_set_cg, "r = np.where(S, A * conv(t), 0.0)", "r = A * conv(t)")
+    for fn, ok in ((oracle_mod.fixed_set_cg, True), (bad, False)):
+        p = fn(A, conv, c, S, np.zeros((n, n)), tol=1e-14, max_iter=500).p.ravel()
+        good = np.allclose(p[s], ref, rtol=1e-10, atol=1e-13) and np.all(p[~s] == 0)
+        assert good == ok
+
+
+def test_alpha_in_the_hertz_numerator_is_caught(oracle_mod):
+    # reading R6: alpha divides Eq. 16; printed in the numerator, the closed form
+    # no longer matches the BEM force of the same graded Hertz contact
+    from oracle import closed_forms as CF
+    bad = _mutant(CF.hertz_force, "4.0 * E0 * a ** (3.0 + k) / (alpha(k, nu) * gamma_pair(k)",
+                  "4.0 * E0 * alpha(k, nu) * a ** (3.0 + k) / (gamma_pair(k)")
+    n, k, nu, d = 32, 0.5, 0.3, 0.01
+    dx = 1.0 / n
+    A = oracle_mod.compliance(k, nu)
+    conv = oracle_mod.FFTConvolver(oracle_mod.influence_quarter(k, dx, dx, n + 1, n + 1), n, n)
+    F = dx * dx * oracle_mod.pk_solve(A, conv, I.paraboloid(n), d).p.sum()
+    a = CF.hertz_radius(d, k, 1.0)
+    assert abs(F / CF.hertz_force(a, k, nu, 1.0) - 1) < 0.02
+    assert abs(F / bad(a, k, nu, 1.0) - 1) > 0.5
