@@ -272,6 +272,29 @@ def test_config1_deflection_eq14(oracle_mod, config1):
     assert CF.hertz_deflection(np.array([0.0]), a, c["k"], c["R"])[0] == pytest.approx(c["d"])
 
 
+@pytest.mark.parametrize("k,n", [(0.5, 64), (-0.5, 128)])
+def test_pressure_profiles_match_bem(oracle_mod, k, n):
+    # The graded Hertz pressure 2 cos(pi k/2) (a^2 - r^2)^((1+k)/2) / ((1+k)^2 R pi^2 A)
+    # and the flat-punch pressure p0 (1 - r^2/a^2)^(-(1-k)/2) against the BEM pressure
+    # field, away from the contact edge where the discretisation smears the profile.
+    from oracle import closed_forms as CF
+    nu, d = 0.3, 0.01
+    dx = 1.0 / n
+    A = oracle_mod.compliance(k, nu)
+    conv = oracle_mod.FFTConvolver(oracle_mod.influence_quarter(k, dx, dx, n + 1, n + 1), n, n)
+    r = I.radius_grid(n, n, dx)
+    p = oracle_mod.pk_solve(A, conv, I.paraboloid(n), d, tol=1e-10).p
+    a = CF.hertz_radius(d, k, 1.0)
+    ref = CF.hertz_pressure(r, a, k, nu, 1.0)
+    sel = r < 0.7 * a
+    assert np.abs(p[sel] - ref[sel]).max() <= 0.01 * ref.max()
+    ap = 0.2
+    p = oracle_mod.pk_solve(A, conv, I.flat_punch(n, ap), d, tol=1e-10).p
+    ref = CF.flat_punch_pressure(r, ap, d, k, nu)
+    sel = r < 0.5 * ap
+    assert np.abs(p[sel] - ref[sel]).max() <= 0.03 * ref[sel].min()
+
+
 def test_pressure_fields_integrate_to_forces(oracle_mod):
     from oracle import closed_forms as CF
     for k in (-0.6, 0.0, 0.4):
