@@ -215,19 +215,34 @@ def torus_kernel(Kq: np.ndarray, py: int, px: int) -> np.ndarray:
 class FFTConvolver:
     """u = K * p by FFT on the zero-padded (2ny) x (2nx) torus (Eq. 13).
 
-    numpy's FP64 FFT is the library step; the spectrum FFT(K) is taken once.
-    Kq must cover offsets 0..ny and 0..nx.
+    A library FP64 FFT is the step: numpy's by default, scipy.fft's with
+    `workers` threads when workers != 1 (the same real 2D transforms, run on
+    several host cores).  The spectrum FFT(K) is taken once.  Kq must cover
+    offsets 0..ny and 0..nx.
     """
 
-    def __init__(self, Kq: np.ndarray, ny: int, nx: int):
+    def __init__(self, Kq: np.ndarray, ny: int, nx: int, workers: int = 1):
         self.ny, self.nx = ny, nx
         self.py, self.px = 2 * ny, 2 * nx
-        self.khat = np.fft.rfft2(torus_kernel(Kq, self.py, self.px))
+        self.workers = workers
+        self.khat = self._rfft2(torus_kernel(Kq, self.py, self.px))
+
+    def _rfft2(self, x):
+        if self.workers == 1:
+            return np.fft.rfft2(x)
+        import scipy.fft
+        return scipy.fft.rfft2(x, workers=self.workers)
+
+    def _irfft2(self, X):
+        if self.workers == 1:
+            return np.fft.irfft2(X, s=(self.py, self.px))
+        import scipy.fft
+        return scipy.fft.irfft2(X, s=(self.py, self.px), workers=self.workers)
 
     def __call__(self, p: np.ndarray) -> np.ndarray:
         pad = np.zeros((self.py, self.px))
         pad[:self.ny, :self.nx] = p
-        u = np.fft.irfft2(np.fft.rfft2(pad) * self.khat, s=(self.py, self.px))
+        u = self._irfft2(self._rfft2(pad) * self.khat)
         return u[:self.ny, :self.nx]
 
 

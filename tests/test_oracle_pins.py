@@ -161,12 +161,13 @@ def test_p_crit_eq24(oracle_mod):
 
 # ---------------------------------------------------------------- Eq. 7 vs Eq. 13
 @pytest.mark.parametrize("ny,nx", [(4, 4), (7, 7), (16, 16), (9, 20), (33, 17)])
-def test_fft_equals_direct(oracle_mod, ny, nx):
+@pytest.mark.parametrize("workers", [1, 4])
+def test_fft_equals_direct(oracle_mod, ny, nx, workers):
     k = -0.4
     Kq = oracle_mod.influence_quarter(k, 1.0 / nx, 1.0 / ny, nx + 1, ny + 1)
     p = I.random_pressure(nx, ny, seed=3)
     ud = oracle_mod.convolve_direct(Kq[:ny, :nx], p)
-    uf = oracle_mod.FFTConvolver(Kq, ny, nx)(p)
+    uf = oracle_mod.FFTConvolver(Kq, ny, nx, workers=workers)(p)
     assert np.abs(ud - uf).max() <= 1e-12 * np.abs(ud).max()
 
 
