@@ -5,38 +5,49 @@ Workload (one "step"): graded half-space k = 0.3, nu = 0.3, E0 = c0 = 1, domain
 side 1 on 2048 x 2048 square elements; rigid paraboloid R = 1 centred;
 non-adhesive preload to d0 = +0.02, then 400 adhesive pull-off steps of
 1.1e-4 (to d = -0.024, past pull-off) with work of adhesion 1e-3 (Sec. 3.1
-algorithm, Eq. 24 with Table 1's c1).  FP32 transform passes, FP64 scalars.
+algorithm, Eq. 24 with Table 1's c1).  Precision FP32 + FP64 refinement (the
+mode whose pressures meet 1e-5 relative L2 against FP64 on every workload):
+FP32 transform passes and fields, FP64 scalars, and every detach round's
+pressure refined against the FP64 residual before the detach decision.
 Inputs are synthetic (the paraboloid), resident in HBM for `value`.
 
-value       : CG iterations of all ranks / max-over-ranks device time (CUDA events)
+value       : CG iterations of all ranks / max-over-ranks device time (CUDA
+              events); every fixed-set CG iteration counts, those of the
+              refinement's correction solves included
 e2e         : the same through the C ABI with pinned host buffers (profile in,
-              pressure out), wall clock around the call
+              per-step results and the final pressure out), wall clock
 roofline    : the dominant transform pass, algorithmic bytes / its live average
               duration (CUDA events recorded inside the captured CG graphs); the
               library counts each timed launch's bytes and flops from the torus
-              and rows that launch worked on (bem_pass_work)
-roofline_full_torus : the same for the passes of a non-adhesive rough-surface
-              solve on the same grid after the timed region, whose overlap set
-              spans the grid: every launch transforms the whole 4096^2 torus
-              (the sweep's solves run on the contact box's smaller torus)
-cpu_baseline: the FP64 oracle (numpy FFT mode) on a bounded sample of the same
-              workload, on this host's cores
+              and rows that launch worked on (bem_pass_work).  `traffic` is the
+              ncu DRAM bytes per launch of that kernel from profiles/, or null
+              when the kernel sources changed since that capture
+plain_fp32  : the same sweep in plain FP32 (no refinement), and how its
+              contact counts and forces compare with the timed sweep's
+full_torus  : the 2048^2 Polonsky-Keer step as the paper applies it, on the whole
+              4096^2 torus: a non-adhesive rough-surface solve whose overlap set
+              spans the grid; CG iterations/s and HBM GB/s at 128 N^2 bytes per
+              iteration (two transforms plus the CG fields), and the FP32 and
+              FP32 + refinement pressures against the FP64 solve's
+cpu_baseline: the FP64 oracle on a bounded sample of the same unit of work
+              (fixed-set CG iterations of an unloading step on the full 2048^2
+              grid, one 4096^2 FFT transform each), on all host cores
 
-batch       : (rank 0, one GPU) the seeded batch mix of independent solves
+batch       : (rank 0, one GPU) the seeded mix of 256 independent solves
               through the native request server at FP32 + FP64 refinement,
-              against the plain FP64 path one solve at a time; solves/s and
-              the largest final-pressure difference between the two
-serving     : the Poisson request stream (200/s) through the server and through
-              the plain FP64 path: solves/s and p50/p99 latency from arrival
+              against the plain FP64 path one solve at a time
+serving     : the Poisson request stream (200/s) through the server, and the
+              plain FP64 path on its first requests: solves/s, p50/p99 latency
 rough_4096  : (rank 0) the 4096^2 non-adhesive rough-surface solve on the 8192^2
-              torus in each precision: CG iterations/s, contact fraction, force,
-              and the passes' durations and bandwidth
+              torus in each precision
 
---impl reference times the oracle alone (rank 0) and prints its own line.
+--impl reference times the oracle alone (rank 0) on the same unit of work and
+prints its own line.
 """
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -60,6 +71,10 @@ NSTEPS = 400
 WORKLOAD = "adhesive paraboloid load-unload 2048x2048 (k=0.3, nu=0.3, R=1, dgamma=1e-3, d0=0.02, 400 steps of 1.1e-4)"
 METRIC = "CG iterations/s, adhesive 2048^2 load-unload sweep"
 UNIT = "iter/s"
+# the unit of work both arms count: one fixed-set CG iteration of the sweep
+UNIT_OF_WORK = "fixed-set CG iteration of the sweep's held-set solves (one 2048^2 FFT convolution each)"
+L2_NOTE = "flushed between steps (256 MiB device write); the host arm has no device cache"
+ORACLE_ITERS = 3  # oracle fixed-set CG iterations per reference step
 
 
 def d_steps(nsteps=NSTEPS):
@@ -150,12 +165,27 @@ def aggregate(elapsed_s, iters, world, device):
     return float(el.item()), float(it.item())
 
 
+def shared_config(world):
+    """The `config` both arms print (same workload, grid and unit of work)."""
+    return {"workload": WORKLOAD, "grid": [N, N], "unit_of_work": UNIT_OF_WORK,
+            "parallelism": f"replicas x{world}", "l2": L2_NOTE}
+
+
+def oracle_sample_desc(cores):
+    return (f"{ORACLE_ITERS} fixed-set CG iterations (Sec. 3.1 held-set solve) per step at the first "
+            "unloading depth of the 2048^2 sweep, on the full 4096^2 torus (oracle FFT mode, FP64, "
+            f"scipy.fft on {cores} threads); held set = the preload's contact disc of the closed-form "
+            "radius (Eq. 15), start p = 0; the initial residual transform is timed apart and excluded")
+
+
 def run_reference(args, rank, world):
+    """The oracle, as it stands, on the same unit of work as the GPU arm."""
     if rank != 0:
         return 0
+    cores = os.cpu_count() or 1
     per = []
     for s in range(args.warmup + args.steps):
-        it, el, _ = cpu_oracle_sample_cached(2)
+        it, el = oracle_fixed_set_sample(ORACLE_ITERS, cores)
         if s >= args.warmup:
             per.append((it, el))
     its = sum(i for i, _ in per)
@@ -164,13 +194,9 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "precision": "fp64 (oracle)",
-                                            "grid": [N, N], "torus": [2 * N, 2 * N],
-                                            "parallelism": "rank 0 only", "l2": "n/a (host)"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "2 Polonsky-Keer CG iterations of the 2048^2 preload per step "
-                                       "(oracle FFT mode, numpy pocketfft FP64, single thread)",
-                             "host": host_cpu()},
+            "data": "synthetic", "precision": "fp64 (oracle)", "config": shared_config(world),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": oracle_sample_desc(cores), "host": host_cpu()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -179,19 +205,30 @@ def run_reference(args, rank, world):
 _ORACLE_CACHE = {}
 
 
-def cpu_oracle_sample_cached(iters):
+def oracle_fixed_set_sample(iters, workers):
+    """(iterations, seconds) of the oracle's fixed-set CG (Sec. 3.1) on the full
+    2048^2 grid at the first unloading depth; the set-up residual transform is
+    timed separately and subtracted."""
     import oracle
     from paper_1612_08395_gb300 import inputs
-    if "conv" not in _ORACLE_CACHE:
+    key = ("conv", workers)
+    if key not in _ORACLE_CACHE:
         dx = 1.0 / N
         Kq = oracle.influence_quarter(K_EXP, dx, dx, N + 1, N + 1)
-        _ORACLE_CACHE["conv"] = oracle.FFTConvolver(Kq, N, N)
-    conv = _ORACLE_CACHE["conv"]
+        _ORACLE_CACHE[key] = oracle.FFTConvolver(Kq, N, N, workers=workers)
+    conv = _ORACLE_CACHE[key]
     A = oracle.compliance(K_EXP, NU, E0, C0)
     h = inputs.paraboloid(N, R)
+    a0 = oracle.closed_forms.hertz_radius(D0, K_EXP, R)
+    S = inputs.radius_grid(N, N, 1.0 / N) <= a0
+    c = h - (D0 - DD)
+    p0 = np.zeros_like(h)
     t0 = time.perf_counter()
-    res = oracle.pk_solve(A, conv, h, D0, tol=1e-300, max_iter=iters)
-    return res.iterations, time.perf_counter() - t0, 0.0
+    oracle.fixed_set_cg(A, conv, c, S, p0, tol=0.0, max_iter=0)
+    t1 = time.perf_counter()
+    res = oracle.fixed_set_cg(A, conv, c, S, p0, tol=0.0, max_iter=iters)
+    t2 = time.perf_counter()
+    return res.iterations, max((t2 - t1) - (t1 - t0), 1e-9)
 
 
 def host_cpu():
@@ -260,16 +297,19 @@ def _served(bem, jobs, arrays, workers, budget, arrivals=None, precision="fp32_r
             sub_late[tag] = (time.perf_counter() - t0 - (arrivals[i] if arrivals is not None else 0.0), i)
         comps += srv.drain(1800.0)
         el = time.perf_counter() - t0
-    lat = [c["t_end"] - c["t_submit"] + sub_late[c["tag"]][0] for c in comps]
+    # latency of each request, in request order
+    lat = [c["t_end"] - c["t_submit"] + sub_late[c["tag"]][0]
+           for c in sorted(comps, key=lambda c: sub_late[c["tag"]][1])]
     bad = [c["status"] for c in comps if c["status"] != 0]
     iters = sum(sum(r.iterations for r in c["results"]) for c in comps)
     return el, lat, iters, bad
 
 
-def batch_and_serving(bem, inputs, n_batch, n_serve, workers):
+def batch_and_serving(bem, inputs, n_batch, n_serve, n_serve_plain, workers):
     """Many independent solves: the seeded batch mix (grid sides 128..1024) and a
     Poisson request stream (rate 200/s, sides 64..2048), each through the server
-    at FP32 + FP64 refinement and through the plain FP64 path one at a time."""
+    at FP32 + FP64 refinement and through the plain FP64 path one at a time (the
+    stream's plain path on its first n_serve_plain requests)."""
     budget = 150 << 30
     out = {}
     if n_batch:
@@ -281,7 +321,7 @@ def batch_and_serving(bem, inputs, n_batch, n_serve, workers):
         rel = [float(np.linalg.norm(x[2] - y[2]) / np.linalg.norm(y[2])) for x, y in zip(a32, a64)
                if np.linalg.norm(y[2]) > 0]
         out["batch"] = {
-            "workload": f"first {n_batch} of 256 seeded solves: side uniform in {{128,256,512,1024}}, "
+            "workload": f"{n_batch} of the 256 seeded solves: side uniform in {{128,256,512,1024}}, "
                         "k~U[-0.8,0.8], nu=0.3, paraboloid or rough, half adhesive (9-step unload)",
             "solves": n_batch, "solves_per_s": n_batch / el, "cg_iterations_per_s": it32 / el,
             "precision": "fp32_refine", "workers": workers, "failed": bad,
@@ -293,14 +333,16 @@ def batch_and_serving(bem, inputs, n_batch, n_serve, workers):
         arr = [r["arrival"] for r in reqs]
         a32 = _job_arrays(inputs, reqs)
         el, lat, it32, bad = _served(bem, reqs, a32, workers, budget, arrivals=arr)
-        el64, lat64, _ = _plain_fp64(bem, reqs, a32, arrivals=arr)
+        m = min(n_serve_plain, n_serve)
+        el64, lat64, _ = _plain_fp64(bem, reqs[:m], a32[:m], arrivals=arr[:m])
         out["serving"] = {
             "workload": f"{n_serve} requests, Poisson arrivals at 200/s (seed 5), side "
                         "round(exp(U[ln 64, ln 2048])), k~U[-0.8,0.8], half adhesive; HBM budget 150 GB",
             "requests": n_serve, "solves_per_s": n_serve / el, "p50_ms": 1e3 * _pct(lat, 50),
-            "p99_ms": 1e3 * _pct(lat, 99), "precision": "fp32_refine", "workers": workers,
-            "failed": bad, "latency": "completion minus arrival",
-            "plain_fp64": {"solves_per_s": n_serve / el64, "p50_ms": 1e3 * _pct(lat64, 50),
+            "p99_ms": 1e3 * _pct(lat, 99), "max_ms": 1e3 * max(lat), "precision": "fp32_refine",
+            "workers": workers, "failed": bad, "latency": "completion minus arrival",
+            "first_requests": {"n": m, "p50_ms": 1e3 * _pct(lat[:m], 50), "p99_ms": 1e3 * _pct(lat[:m], 99)},
+            "plain_fp64": {"requests": m, "solves_per_s": m / el64, "p50_ms": 1e3 * _pct(lat64, 50),
                            "p99_ms": 1e3 * _pct(lat64, 99)}}
     return out
 
@@ -348,24 +390,105 @@ def rough_4096(bem, inputs, torch, precisions=("fp32", "fp32_refine", "fp64")):
     return {"rough_4096": out}
 
 
+def kernel_sources_sha():
+    """sha256 of the transform kernels' sources (a traffic figure from profiles/
+    is used only while they are unchanged)."""
+    import hashlib
+    hs = hashlib.sha256()
+    for f in ("conv_kernels.cuh", "common.cuh", "geo_table.h", "bem_impl.h"):
+        with open(os.path.join(ROOT, "paper_1612_08395_gb300", "csrc", f), "rb") as fh:
+            hs.update(fh.read())
+    return hs.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_key):
+    """ncu DRAM bytes per launch recorded in profiles/traffic_*.md for this kernel
+    (lines `kernel_key:`, `source_sha16:`, `dram_bytes_per_launch:`), or None if
+    absent or taken on other kernel sources."""
+    import glob
+    sha = kernel_sources_sha()
+    for f in sorted(glob.glob(os.path.join(ROOT, "profiles", "traffic_*.md"))):
+        kv = {}
+        with open(f) as fh:
+            for line in fh:
+                if ":" in line and not line.startswith(("#", "|", " ")):
+                    k, v = line.split(":", 1)
+                    kv[k.strip().lstrip("- ").strip("`")] = v.strip().strip("`")
+        if kv.get("kernel_key") == kernel_key and kv.get("source_sha16") == sha:
+            try:
+                return float(kv["dram_bytes_per_launch"]), os.path.basename(f)
+            except (KeyError, ValueError):
+                return None, None
+    return None, None
+
+
+def full_torus_leg(bem, inputs, torch, hd, stream, hbm):
+    """The 2048^2 Polonsky-Keer step on the whole 4096^2 torus: a non-adhesive
+    rough-surface solve (config 3b's recipe at 2048^2, d = rms height) whose
+    overlap set spans the grid, in FP32, FP32 + refinement and FP64."""
+    rough_h, rough_d = inputs.rough_self_affine(N, hurst=0.8, q1_over_q0=256.0, rms_slope=0.1, seed=1612)
+    rough_dev = torch.from_numpy(rough_h).cuda()
+    out = {"workload": "non-adhesive self-affine rough surface (H=0.8, q1/q0=256, rms slope 0.1, seed 1612) "
+                       "at d = rms height, 2048^2 grid, 4096^2 torus",
+           "bytes_per_iteration": 128.0 * N * N,
+           "bytes_model": "128 N^2: two transforms (44 N^2 each) and the CG fields (40 N^2), FP32"}
+    ps = {}
+    for prec in ("fp32", "fp32_refine", "fp64"):
+        p = torch.empty((N, N), dtype=torch.float64, device="cuda")
+        hd.solve(rough_dev, rough_d, pressure_out=p, precision=prec, stream=stream)  # warm-up
+        torch.cuda.synchronize()
+        hd.pass_times(reset=True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res, rc = hd.solve(rough_dev, rough_d, pressure_out=p, precision=prec, stream=stream,
+                           time_passes=prec == "fp32")
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        ent = {"iterations": res.iterations, "ms": ms, "iter_per_s": 1e3 * res.iterations / ms,
+               "contact_fraction": res.contact_count / (N * N), "force": res.force, "status": rc}
+        if prec == "fp32":
+            ent["hbm_gbs"] = ent["iter_per_s"] * out["bytes_per_iteration"] / 1e9
+            ent["hbm_frac"] = ent["hbm_gbs"] / hbm
+            wb, _ = hd.pass_work()
+            pms, pn, _ = hd.pass_times(reset=True)
+            if pn:
+                avg = [m / pn for m in pms]
+                ent["pass_us"] = {k: 1e3 * v for k, v in zip("ABC", avg)}
+                ent["pass_gbs"] = {k: b / (v * 1e-3) / 1e9 for k, b, v in zip("ABC", wb, avg)}
+                ent["pass_hbm_frac"] = {k: g / hbm for k, g in ent["pass_gbs"].items()}
+        ps[prec] = p.cpu().numpy()
+        out[prec] = ent
+    ref = ps["fp64"]
+    for prec in ("fp32", "fp32_refine"):
+        out[prec]["pressure_rel_l2_vs_fp64"] = float(np.linalg.norm(ps[prec] - ref) / np.linalg.norm(ref))
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_refine", "fp64"])
+    ap.add_argument("--precision", default="fp32_refine", choices=["fp32", "fp32_refine", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep-steps", type=int, default=NSTEPS,
                     help="unloading steps per sweep (400 = the workload; fewer only for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--batch-jobs", type=int, default=64,
+    ap.add_argument("--e2e-steps", type=int, default=2, help="sweeps timed through the C ABI with host buffers")
+    ap.add_argument("--batch-jobs", type=int, default=256,
                     help="solves of the batch mix to time (256 = the whole mix; 0 = skip)")
-    ap.add_argument("--serve-requests", type=int, default=32,
+    ap.add_argument("--serve-requests", type=int, default=128,
                     help="requests of the Poisson stream to serve (0 = skip)")
+    ap.add_argument("--serve-plain", type=int, default=32,
+                    help="of those, how many the plain FP64 path serves for comparison")
     ap.add_argument("--workers", type=int, default=8, help="server worker streams")
     ap.add_argument("--no-rough-4096", action="store_true",
                     help="skip the 4096^2 rough-surface solves reported after the timed region")
+    ap.add_argument("--no-side-legs", action="store_true",
+                    help="skip plain_fp32 and full_torus (profiling runs only)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -393,15 +516,14 @@ def main():
 
     h = bem.Handle(N, N, dx, dx, K_EXP, NU, E0, C0)
     info = h.info()
-    opts = dict(precision=args.precision, stream=stream)
 
-    def one_step(timed_passes=False):
-        res, rc = h.sweep(prof_d, ds, dgamma=DGAMMA, final_pressure=p_d, time_passes=timed_passes,
-                          **opts)
+    def one_sweep(precision, timed_passes=False, prof=prof_d, out=p_d, use_stream=True):
+        res, rc = h.sweep(prof, ds, dgamma=DGAMMA, final_pressure=out, time_passes=timed_passes,
+                          precision=precision, stream=stream if use_stream else None)
         return res
 
     for _ in range(args.warmup):
-        one_step()
+        one_sweep(args.precision)
     torch.cuda.synchronize()
 
     # timed region
@@ -420,7 +542,7 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        results = one_step(timed_passes=True)
+        results = one_sweep(args.precision, timed_passes=True)
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
@@ -437,12 +559,12 @@ def main():
     # e2e through the C ABI with pinned host buffers
     prof_pin = torch.from_numpy(prof_h).pin_memory()
     out_pin = torch.empty((N, N), dtype=torch.float64).pin_memory()
+    e2e_steps = 0 if args.no_e2e else max(1, min(args.e2e_steps, args.steps))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e2e_iters = 0
-    for _ in range(0 if args.no_e2e else args.steps):
-        res, rc = h.sweep(prof_pin, ds, dgamma=DGAMMA, final_pressure=out_pin,
-                          precision=args.precision)
+    for _ in range(e2e_steps):
+        res = one_sweep(args.precision, prof=prof_pin, out=out_pin, use_stream=False)
         e2e_iters += sum(r.iterations for r in res)
     e2e_s = time.perf_counter() - t0
     e2e_val = e2e_iters / e2e_s if e2e_iters else None
@@ -456,49 +578,54 @@ def main():
     bytes_dom = work_bytes[dom]
     flops_dom = work_flops[dom]
     achieved = bytes_dom / (avg_ms[dom] * 1e-3) / 1e9
-
-    # the full 4096^2 torus: passes of a non-adhesive rough-surface solve (its
-    # overlap set {h <= d} spans the grid, so every iteration transforms the
-    # whole torus), timed the same way, outside the timed region
-    rough_h, rough_d = inputs.rough_self_affine(N, hurst=0.8, q1_over_q0=256.0, rms_slope=0.1, seed=1612)
-    rough_dev = torch.from_numpy(rough_h).cuda()
-    h.pass_times(reset=True)
-    for _ in range(2):
-        h.solve(rough_dev, rough_d, precision=args.precision, stream=stream, time_passes=True)
-    torch.cuda.synchronize()
-    fb, _ = h.pass_work()
-    fms, fn, _ = h.pass_times(reset=True)
-    favg = [m / max(fn, 1) for m in fms]
-    fdom = int(np.argmax(favg))
-    full = {"kernel": f"pass {names[fdom]}", "bound": "hbm",
-            "achieved": fb[fdom] / (favg[fdom] * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
-            "frac": fb[fdom] / (favg[fdom] * 1e-3) / 1e9 / hbm,
-            "avg_ms": {k: v for k, v in zip(names, favg)}, "bytes_per_launch": fb[fdom],
-            "timed_launches": fn,
-            "workload": "non-adhesive self-affine rough surface (H=0.8, q1/q0=256, rms slope 0.1, "
-                        "seed 1612) at d = rms height, 2048^2 grid, 4096^2 torus"}
+    kernel_key = f"pass {names[dom]}, fixed-set loop, FP32, box torus of the 2048^2 sweep"
+    traffic, traffic_src = profiled_traffic(kernel_key)
 
     forces = [r.force for r in results]
     counts = [r.contact_count for r in results]
     last_contact = max((i for i, c in enumerate(counts) if c > 0), default=0)
-    if args.sweep_steps != NSTEPS:
-        line_note = f"profiling run: {args.sweep_steps} unloading steps, not the workload"
-    else:
-        line_note = None
+    sweep = {"precision": args.precision, "torus": [info.Px, info.Py],
+             "fp32_shapes": {"rows_per_cta": info.rows_per_cta, "cols_per_cta": info.cols_per_cta},
+             "sweep_s": elapsed / args.steps, "cg_iterations_per_step": iters_total / args.steps,
+             "detach_rounds": int(sum(r.detach_rounds for r in results)),
+             "stalled_solves": int(sum(r.stalled for r in results)),
+             "pull_off_force": min(forces), "last_contact_depth": float(ds[last_contact]),
+             "preload_force": forces[0], "preload_contact_count": counts[0]}
+
+    side = {}
+    if rank == 0 and not args.no_side_legs:
+        # plain FP32 sweep: speed, and agreement with the timed (refined) sweep
+        p32 = torch.empty_like(p_d)
+        one_sweep("fp32", out=p32)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r32 = one_sweep("fp32", out=p32)
+        e1.record(stream)
+        e1.synchronize()
+        ms32 = e0.elapsed_time(e1)
+        it32 = sum(r.iterations for r in r32)
+        fmax = max(abs(f) for f in forces)
+        side["plain_fp32"] = {
+            "sweep_s": ms32 / 1e3, "cg_iterations": it32, "iter_per_s": 1e3 * it32 / ms32,
+            "steps_with_other_contact_count": int(sum(a.contact_count != b.contact_count
+                                                      for a, b in zip(r32, results))),
+            "max_force_diff_over_max_force": max(abs(a.force - b.force) for a, b in zip(r32, results)) / fmax,
+            "compared_with": args.precision}
+        side["full_torus"] = full_torus_leg(bem, inputs, torch, h, stream, hbm)
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * elapsed_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if args.precision != "fp64" else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": args.precision, "grid": [N, N],
-                   "torus": [info.Px, info.Py], "parallelism": f"replicas x{world}",
-                   "fp32_shapes": {"rows_per_cta": info.rows_per_cta, "cols_per_cta": info.cols_per_cta},
-                   "l2": "flushed between steps (256 MiB write)",
-                   "cg_iterations_per_step": iters_total / args.steps,
-                   "pull_off_force": min(forces), "last_contact_depth": float(ds[last_contact]),
-                   "preload_force": forces[0], "preload_contact_count": counts[0]},
+        "dtype": "f32+f64" if args.precision == "fp32_refine" else ("f32" if args.precision == "fp32" else "f64"),
+        "data": "synthetic", "precision": args.precision,
+        "config": shared_config(world),
+        "sweep": sweep,
         "roofline": {"kernel": f"pass {names[dom]}", "bound": "hbm", "achieved": achieved,
-                     "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                     "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
+                     "traffic_source": traffic_src, "kernel_key": kernel_key,
                      "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
                      "avg_ms": {k: v for k, v in zip(names, avg_ms)}, "timed_launches": pass_n,
                      "bytes_per_launch": bytes_dom,
@@ -508,26 +635,31 @@ def main():
                              "frac": flops_dom / (avg_ms[dom] * 1e-3) / 1e12
                              / fp32_peak_tflops(clocks.get("sm_max_mhz")),
                              "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}},
-        "roofline_full_torus": full,
         "clocks": clocks,
-        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 8 * N * N + 8 * len(ds),
-                "d2h_bytes_per_step": 8 * N * N + 56 * len(ds)},
+        "e2e": {"value": e2e_val, "unit": UNIT, "steps": e2e_steps,
+                "h2d_bytes_per_step": 8 * N * N + 8 * len(ds),
+                "d2h_bytes_per_step": 8 * N * N + ctypes.sizeof(bem.Result) * len(ds)},
         "gpu_launches": int(launches),
     }
-    if line_note:
-        line["note"] = line_note
+    line.update(side)
+    if args.sweep_steps != NSTEPS:
+        line["note"] = f"profiling run: {args.sweep_steps} unloading steps, not the workload"
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        it, el, _ = cpu_oracle_sample_cached(3)
-        line["cpu_baseline"] = {"value": it / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": "3 Polonsky-Keer CG iterations of the 2048^2 preload solve "
-                                          "(oracle FFT mode, numpy pocketfft FP64, single thread)",
-                                "host": host_cpu()}
+        cores = os.cpu_count() or 1
+        its, el = 0, 0.0
+        for _ in range(2):
+            i1, e1_ = oracle_fixed_set_sample(ORACLE_ITERS, cores)
+            its += i1
+            el += e1_
+        line["cpu_baseline"] = {"value": its / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": "2 x " + oracle_sample_desc(cores), "host": host_cpu()}
     h.close()
     del l2_flush
     if rank == 0 and world == 1 and not args.no_rough_4096:
         line.update(rough_4096(bem, inputs, torch))
     if rank == 0 and world == 1 and (args.batch_jobs or args.serve_requests):
-        line.update(batch_and_serving(bem, inputs, args.batch_jobs, args.serve_requests, args.workers))
+        line.update(batch_and_serving(bem, inputs, args.batch_jobs, args.serve_requests, args.serve_plain,
+                                      args.workers))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -48,8 +48,9 @@ extern "C" {
 #define BEM_PREC_FP32_REFINE 2
 
 /* Record CUDA events around the three transform passes of the first CG
- * iteration of every fourth captured chunk of 8 iterations, the first chunk of
- * every solve included (read back with bem_pass_times). */
+ * iteration of every CG solve: each solve then starts with a captured chunk of
+ * 8 iterations carrying the event records before its device-driven loop
+ * continues (read back with bem_pass_times). */
 #define BEM_FLAG_TIME_PASSES 1
 
 typedef struct bem_ctx *bem_handle;
@@ -74,6 +75,10 @@ typedef struct {
   int detach_rounds;        /* adhesive: detach-and-resolve rounds                 */
   int contact_count;        /* elements in contact                                 */
   int status;               /* BEM_OK or BEM_ENOCONV / BEM_ENUMERIC                */
+  int stalled;              /* CG solves of this step that stopped because their
+                               stopping measure found no new minimum for 200
+                               iterations (the arithmetic's rounding floor) while
+                               still above the tolerance; counted as converged    */
 } bem_result;
 
 /* ---------------------------------------------------------------------------
@@ -193,11 +198,36 @@ typedef struct {
   long long tag;
   int status;
   double t_submit, t_start, t_end;
+  int device;  /* CUDA device the job ran on (-1: cancelled before it started) */
 } bem_completion;
 
 typedef struct bem_server *bem_server_handle;
 
+/* bem_server_create: nworkers workers on the current device.
+ * bem_server_create_on: workers_per_device workers on each of the ndev listed
+ *   devices, each device with its own budget of hbm_budget_per_device bytes and
+ *   its own handle cache.  A job runs wholly on one device (independent solves
+ *   need no exchange between devices); bem_server_place decides which. */
 int bem_server_create(int nworkers, size_t hbm_budget_bytes, bem_server_handle *out);
+int bem_server_create_on(int ndev, const int *devices, int workers_per_device,
+                         size_t hbm_budget_per_device, bem_server_handle *out);
+
+/* Placement of one job across devices (host-only; the server calls it for
+ * every queued job, and it is exported so the policy can be checked without a
+ * GPU).  views[i] describes device i: its budget, the bytes accounted to it
+ * (running jobs and cached handles), of those the bytes of idle cached handles
+ * that may be evicted (evictable) and, when it holds an idle cached handle for
+ * the job's spectrum key, that handle's bytes (has_cached, cached_bytes), and
+ * its idle workers.  A device qualifies when it has an idle worker and the job
+ * (need bytes, less its cached handle's) fits its budget once idle handles are
+ * evicted.  Among those it prefers one with a cached handle, then the one with
+ * the most budget left after the job, then the lower index.  Returns the
+ * device's position in views, or -1 when none qualifies now. */
+typedef struct {
+  size_t budget, used, evictable, cached_bytes;
+  int idle_workers, has_cached;
+} bem_device_view;
+int bem_server_place(int ndev, const bem_device_view *views, size_t need);
 int bem_server_submit(bem_server_handle s, const bem_job *job);
 int bem_server_poll(bem_server_handle s, bem_completion *out, int max, int wait_ms);
 int bem_server_cancel(bem_server_handle s, long long tag);
@@ -262,12 +292,12 @@ int bem_pass_work(bem_handle h, double bytes[3], double flops[3]);
 /* ---------------------------------------------------------------------------
  * bem_convolve_noalloc: u = A K*p in FP64 for callers that must not allocate
  * device memory.  The paper has no counterpart; this is a service of the
- * library.  Callers that cannot call cudaMalloc -- code running while a stream
- * is captured into a CUDA graph, hosts whose device memory belongs to a pool
- * they must not bypass, loops that cannot afford cudaMalloc's device-wide
- * synchronisation -- get the same transform as bem_convolve(FP64) without a
- * handle and without any allocation: its scratch is a 2 MiB static device
- * array that every GPU loading the library holds until exit.
+ * library.  Callers that cannot call cudaMalloc -- hosts whose device memory
+ * belongs to a caching allocator or arena they must not bypass, loops that
+ * cannot afford cudaMalloc's device-wide synchronisation -- get the same
+ * transform as bem_convolve(FP64) without a handle and without any
+ * allocation: its scratch is a 2 MiB static device array that every GPU
+ * loading the library holds until exit.
  *   khat       : device pointer, the FP64 spectrum quarter exactly as
  *                bem_spectrum writes it for a handle of the same Nx, Ny
  *                ((Py/2+1) rows of Px/2+1 values)
@@ -275,12 +305,15 @@ int bem_pass_work(bem_handle h, double bytes[3], double flops[3]);
  *   compliance : A = alpha (1-nu^2) c0^k / E0 (bem_get_info().compliance)
  *   p, u       : device pointers to Nx*Ny FP64 fields (input, output)
  *   stream     : cudaStream_t to run on (NULL = legacy default stream)
- * The call is asynchronous on `stream`.  Its first call on a device looks up
- * the static array's device address; make that first call before any stream
- * capture.  All calls share the array: calls whose work overlaps on the GPU
- * race and must be serialised by the caller.  Returns BEM_EINVAL for sizes
- * beyond the maximum, host pointers or NULL arguments, BEM_ECUDA on a launch
- * failure. */
+ * The call is asynchronous on `stream` and uses the launch shapes a handle of
+ * the same grid uses.  Its first call on a device does a one-time set-up with
+ * that device current: it opts the transform kernels into the shared memory
+ * they need (as bem_create does) and looks up the static array's device
+ * address; make that first call before any stream capture.  All calls share
+ * the array and it keeps the last call's contents: calls whose work overlaps
+ * on the GPU race and must be serialised by the caller.  Returns BEM_EINVAL
+ * for sizes beyond the maximum, host pointers or NULL arguments, BEM_ECUDA on
+ * a set-up or launch failure. */
 int bem_convolve_noalloc(const double *khat, int Nx, int Ny, double compliance, const double *p,
                          double *u, void *stream);
 

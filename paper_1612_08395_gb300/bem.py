@@ -52,7 +52,7 @@ class Result(ctypes.Structure):
                 ("contact_radius", ctypes.c_double), ("final_eps", ctypes.c_double),
                 ("max_gap_violation", ctypes.c_double), ("depth", ctypes.c_double),
                 ("iterations", ctypes.c_int), ("detach_rounds", ctypes.c_int),
-                ("contact_count", ctypes.c_int), ("status", ctypes.c_int)]
+                ("contact_count", ctypes.c_int), ("status", ctypes.c_int), ("stalled", ctypes.c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -78,7 +78,13 @@ class Job(ctypes.Structure):
 
 class Completion(ctypes.Structure):
     _fields_ = [("tag", ctypes.c_longlong), ("status", ctypes.c_int), ("t_submit", ctypes.c_double),
-                ("t_start", ctypes.c_double), ("t_end", ctypes.c_double)]
+                ("t_start", ctypes.c_double), ("t_end", ctypes.c_double), ("device", ctypes.c_int)]
+
+
+class DeviceView(ctypes.Structure):
+    _fields_ = [("budget", ctypes.c_size_t), ("used", ctypes.c_size_t), ("evictable", ctypes.c_size_t),
+                ("cached_bytes", ctypes.c_size_t), ("idle_workers", ctypes.c_int),
+                ("has_cached", ctypes.c_int)]
 
 
 _lib = None
@@ -119,6 +125,9 @@ def load_library(path: str = LIB_PATH):
     lib.bem_p_crit.argtypes = [ctypes.c_double] * 6
     lib.bem_set_material.argtypes = [vp] + [ctypes.c_double] * 3
     lib.bem_server_create.argtypes = [ip, ctypes.c_size_t, ctypes.POINTER(vp)]
+    lib.bem_server_create_on.argtypes = [ip, ctypes.POINTER(ctypes.c_int), ip, ctypes.c_size_t,
+                                         ctypes.POINTER(vp)]
+    lib.bem_server_place.argtypes = [ip, ctypes.POINTER(DeviceView), ctypes.c_size_t]
     lib.bem_server_submit.argtypes = [vp, ctypes.POINTER(Job)]
     lib.bem_server_poll.argtypes = [vp, ctypes.POINTER(Completion), ip, ip]
     lib.bem_server_pending.argtypes = [vp]
@@ -317,10 +326,16 @@ class Server:
     per-step results and the final pressure (if one was asked for).
     """
 
-    def __init__(self, nworkers=4, hbm_budget_bytes=16 << 30):
+    def __init__(self, nworkers=4, hbm_budget_bytes=16 << 30, devices=None):
+        """nworkers workers on the current device, or (devices = a list of CUDA
+        device indices) nworkers workers and a budget of hbm_budget_bytes on each."""
         lib = load_library()
         s = ctypes.c_void_p()
-        _check(lib.bem_server_create(nworkers, hbm_budget_bytes, ctypes.byref(s)))
+        if devices is None:
+            _check(lib.bem_server_create(nworkers, hbm_budget_bytes, ctypes.byref(s)))
+        else:
+            devs = (ctypes.c_int * len(devices))(*devices)
+            _check(lib.bem_server_create_on(len(devices), devs, nworkers, hbm_budget_bytes, ctypes.byref(s)))
         self._s = s
         self._live = {}
         self._next = 0
@@ -348,7 +363,7 @@ class Server:
         for c in buf[:n]:
             profile, ds, res, fp = self._live.pop(c.tag)
             out.append({"tag": c.tag, "status": c.status, "t_submit": c.t_submit, "t_start": c.t_start,
-                        "t_end": c.t_end, "results": list(res), "final_pressure": fp})
+                        "t_end": c.t_end, "device": c.device, "results": list(res), "final_pressure": fp})
         return out
 
     def cancel(self, tag):
@@ -364,6 +379,12 @@ class Server:
     @staticmethod
     def footprint(nx, ny):
         return load_library().bem_server_footprint(nx, ny)
+
+    @staticmethod
+    def place(views, need):
+        """bem_server_place on a list of dicts with the DeviceView fields."""
+        arr = (DeviceView * len(views))(*[DeviceView(**v) for v in views])
+        return load_library().bem_server_place(len(views), arr, need)
 
     def drain(self, timeout_s=600.0):
         """Poll until every submitted job has completed; returns their completions."""

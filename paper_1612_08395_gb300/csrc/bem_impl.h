@@ -47,11 +47,17 @@ struct Scalars {
   double tau, beta, delta, G, G_old, eps, bnorm, pcrit;
   double sum_p, sum_dp, n_ol, n_ic, str, eps_min;
   int max_iter, iter, done, status, have_tau, it_min;
-  int nA, pad1;   // CTAs of the last pass A launch (its partials feed pass C)
+  int nA;        // CTAs of the last pass A launch (its partials feed pass C)
+  // Debug builds only: 1 = the first persistent pass A launch of the solve
+  // waits on a barrier that nothing completes (tests the bounded wait)
+  int inject;
   // Rows band0 .. band1 and columns col0 .. col1 hold every element of the
   // fixed contact set S (band0 > band1: S is empty); written by k_box at the
   // start of a fixed-set solve.
   int band0, band1, col0, col1;
+  // Device-driven loop: iterations finished inside the captured while-loop
+  // graph, and the cap after which it stops (status SC_NOCONV).
+  int loops, max_loops;
   unsigned int cnt_a, cnt_c, cnt_e, cnt_r;  // last-block arrival counters
   // Sticky device error bits (kept across solves: init_scalars does not copy
   // this member); 1 = a kernel gave up waiting for its own asynchronous copies,
@@ -117,6 +123,10 @@ struct PassArgs {
   Scalars* sc;
   unsigned int* kerr;   // sticky error word (may be null: errors then go unreported)
   int use_band;         // fixed-set CG loop: restrict the passes to rows sc->band0 .. band1
+  // Captured inside the body of a while-loop graph: the thread that finishes an
+  // iteration's scalars sets the loop condition `cond` (continue while not done).
+  int use_cond;
+  unsigned long long cond;  // cudaGraphConditionalHandle
 };
 
 template <typename T> void launch_pass_a(const PassArgs<T>& a, int mode, cudaStream_t s);
@@ -127,7 +137,7 @@ template <typename T> void launch_pass_c(const PassArgs<T>& a, int mode, cudaStr
 template <typename T> void launch_pk_init(const Plan& pl, const double* h64, double d, T* c, T* p,
                                           T* t, int warm, int ngrid, cudaStream_t s);
 template <typename T> void launch_cg_update(const Plan& pl, Fields<T> f, double* part, Scalars* sc,
-                                            int ngrid, cudaStream_t s);
+                                            int ngrid, int use_cond, unsigned long long cond, cudaStream_t s);
 void launch_box(const Plan& pl, const uint8_t* S, Scalars* sc, cudaStream_t s);
 void launch_box_overlap(const Plan& pl, const double* h, double d, Scalars* sc, cudaStream_t s);
 void launch_box_copy64(const double* src, int nx, int ny, int x0, int y0, double* dst, int bx, int by,
@@ -154,6 +164,14 @@ void launch_to_f32(const double* src, float* dst, size_t n, cudaStream_t s);
 void launch_to_f32_scaled(const double* src, double scale, float* dst, size_t n, cudaStream_t s);
 // S = (p > 0) or (g < 0): active set of the refinement sweep.
 void launch_active_set(const double* p, const double* g, uint8_t* S, size_t n, cudaStream_t s);
+
+// The default launch plan of a grid (the one bem_create gives a handle) and
+// whether a plan's shapes are launchable (warps, launch bounds, shared memory).
+Plan default_plan(int nx, int ny, int px, int py, int esize, int nsm);
+bool plan_fits(const Plan& pl, int esize);
+// Once per device (with it current): shared-memory opt-ins of the pass kernels
+// and the quadrature nodes.  Returns BEM_OK or a BEM_E* code with the message set.
+int device_setup(int dev);
 
 // Record `msg` as the thread's last error and return `code`.
 int set_error(int code, const char* msg);

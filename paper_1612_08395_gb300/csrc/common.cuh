@@ -315,7 +315,8 @@ __device__ __forceinline__ constexpr bool bem_check(bool, unsigned int*) { retur
 // ---------------------------------------------------------------------------
 // Bulk asynchronous copies (global -> shared, contiguous, 16-byte aligned and
 // sized) that complete on a shared-memory mbarrier.  Waits are bounded: after
-// kMbarTries unsuccessful polls the caller gets `false` and gives up.
+// kMbarTries unsuccessful polls, or about a second, the caller gets `false`
+// and gives up.
 constexpr int kMbarTries = 1 << 20;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -341,8 +342,16 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
 }
+// Wall-clock bound of one wait (ns of %globaltimer), next to the poll bound.
+constexpr unsigned long long kMbarMaxNs = 1000000000ull;
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
   const unsigned a = smem_u32(bar);
+  unsigned long long t0 = 0;
   for (int i = 0; i < kMbarTries; ++i) {
     unsigned ok;
     asm volatile(
@@ -351,6 +360,8 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
         : "r"(a), "r"(parity)
         : "memory");
     if (ok) return true;
+    if (i == 0) t0 = global_ns();
+    else if ((i & 255) == 0 && global_ns() - t0 > kMbarMaxNs) return false;
   }
   return false;
 }

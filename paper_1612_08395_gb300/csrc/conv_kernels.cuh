@@ -551,8 +551,24 @@ __global__ void BEM_ROWP_BOUNDS(LOGL) k_pass_ap(PassArgs<T> a) {
     const int row0 = g * nb, row = row0 + b;
     const bool act = row < nrows;
     const size_t rowoff = (size_t)row * ncols;
-    const bool ok = mbar_wait(&bar, phase);
+    bool ok = mbar_wait(&bar, phase);
     phase ^= 1u;
+#ifdef BEM_DEBUG_CHECKS
+    // Test hook of debug builds: once per solve whose scalars ask for it, CTA 0
+    // of the first CG-loop launch waits (bounded) on a barrier nothing
+    // completes; every copy it issued has already landed, so it gives up like a
+    // lost copy would.  (A_PLAIN launches carry no scalars.)
+    if (MODE != A_PLAIN && sc != nullptr && g == g0 && blockIdx.x == 0) {
+      __shared__ unsigned long long never;
+      __shared__ int inj;
+      if (tid == 0) {
+        inj = atomicExch(&sc->inject, 0);
+        if (inj) mbar_init(&never, 1);
+      }
+      __syncthreads();
+      if (inj && tid == 0) ok = ok && mbar_wait(&never, 0);
+    }
+#endif
     if (__syncthreads_or(!ok)) {  // the staged rows never arrived: give up together
       if (tid == 0 && a.kerr) atomicOr(a.kerr, 1u);
       return;
@@ -844,11 +860,25 @@ __device__ __forceinline__ void epi_apply(const PassArgs<T>& a, size_t i, T u, c
   }
 }
 
+// Device-driven CG loop (a while-loop node of a CUDA graph): the thread that
+// finishes an iteration's scalars sets the loop condition -- run the body again
+// while the solve is not done.  Every place that can set `done` calls it.
+__device__ __forceinline__ void set_loop_cond(int use, unsigned long long cond, const Scalars* sc) {
+  if (use) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, sc->done ? 0u : 1u);
+}
+// Count an iteration of the device-driven loop; past the cap the solve ends
+// unconverged (a bound on the loop whatever the iteration's outcome).
+__device__ __forceinline__ void count_loop(Scalars* sc) {
+  sc->loops += 1;
+  if (!sc->done && sc->loops >= sc->max_loops) { sc->status = SC_NOCONV; sc->done = 1; }
+}
+
 // Scalar work of the last CTA of a pass-C launch (FP64): the Polonsky-Keer
 // stopping test and beta after the gap pass, tau after the r pass, tau or the
 // initial residual of the fixed-set CG.
 template <int MODE>
-__device__ __forceinline__ void pass_c_finalize(Scalars* sc, const double (&s2)[2], const double (&s3)[3]) {
+__device__ __forceinline__ void pass_c_finalize(Scalars* sc, const double (&s2)[2], const double (&s3)[3],
+                                                int use_cond, unsigned long long cond) {
   if (MODE == C_PK_G) {
     sc->cnt_c = 0;
     const double G = s2[0], nic = s2[1];
@@ -877,6 +907,7 @@ __device__ __forceinline__ void pass_c_finalize(Scalars* sc, const double (&s2)[
       else { sc->beta = sc->delta * G / sc->G_old; sc->G_old = G; }
     }
     if (done) sc->done = 1;
+    set_loop_cond(use_cond, cond, sc);
   } else if (MODE == C_PK_R) {
     sc->cnt_a = 0;
     const double sgt = s2[0], srt = s2[1];
@@ -889,6 +920,8 @@ __device__ __forceinline__ void pass_c_finalize(Scalars* sc, const double (&s2)[
       sc->have_tau = 0;
       sc->delta = 0.0;
     } else { sc->tau = sgt / srt; sc->have_tau = 1; }
+    count_loop(sc);
+    set_loop_cond(use_cond, cond, sc);
   } else if (MODE == C_CG_R) {
     sc->cnt_a = 0;
     const double str = s2[0];
@@ -896,6 +929,7 @@ __device__ __forceinline__ void pass_c_finalize(Scalars* sc, const double (&s2)[
     if (!isfinite(str)) { sc->status = SC_NUMERIC; sc->done = 1; }
     else if (str <= 0.0) { sc->done = 1; }
     else sc->tau = sc->G / str;
+    set_loop_cond(use_cond, cond, sc);
   } else if (MODE == C_CG_G) {
     sc->cnt_a = 0;
     const double G = s2[0];
@@ -1065,7 +1099,7 @@ __global__ void BEM_ROW_BOUNDS(LOGL) k_pass_c(PassArgs<T> a) {
   double s3[3] = {0, 0, 0};
   if (MODE == C_PK_G) sum_partials<3>(a.partA, __ldcg(&sc->nA), s3, red);
   if (tid != 0) return;
-  pass_c_finalize<MODE>(sc, s2, s3);
+  pass_c_finalize<MODE>(sc, s2, s3, a.use_cond, a.cond);
 }
 
 // ---------------------------------------------------------------------------
@@ -1252,7 +1286,7 @@ __global__ void BEM_ROWP_BOUNDS(LOGL) k_pass_cp(PassArgs<T> a) {
   double s3[3] = {0, 0, 0};
   if (MODE == C_PK_G) sum_partials<3>(a.partA, __ldcg(&sc->nA), s3, red);
   if (tid != 0) return;
-  pass_c_finalize<MODE>(sc, s2, s3);
+  pass_c_finalize<MODE>(sc, s2, s3, a.use_cond, a.cond);
 }
 
 // ---------------------------------------------------------------------------
@@ -1306,7 +1340,8 @@ __device__ __forceinline__ T cg_update_one(T* __restrict__ p, T* __restrict__ g,
 // the new G, beta and the convergence test.  Four elements per thread and
 // trip through vector loads when the pointers allow it.
 template <typename T>
-__global__ void k_cg_update(int nx, Fields<T> f, double* part, Scalars* sc) {
+__global__ void k_cg_update(int nx, Fields<T> f, double* part, Scalars* sc, int use_cond,
+                            unsigned long long cond) {
   __shared__ double red[3 * 32];
   __shared__ int lastflag;
   if (sc->done) return;
@@ -1350,11 +1385,17 @@ __global__ void k_cg_update(int nx, Fields<T> f, double* part, Scalars* sc) {
   const double Gn = s[0];
   sc->iter += 1;
   sc->eps = sqrt(Gn) / sc->bnorm;
-  if (!isfinite(Gn)) { sc->status = SC_NUMERIC; sc->done = 1; return; }
-  if (sqrt(Gn) <= sc->tol * sc->bnorm) sc->done = 1;
-  else if (sc->iter >= sc->max_iter) { sc->status = SC_NOCONV; sc->done = 1; }
-  sc->beta = Gn / sc->G;
-  sc->G = Gn;
+  if (!isfinite(Gn)) {
+    sc->status = SC_NUMERIC;
+    sc->done = 1;
+  } else {
+    if (sqrt(Gn) <= sc->tol * sc->bnorm) sc->done = 1;
+    else if (sc->iter >= sc->max_iter) { sc->status = SC_NOCONV; sc->done = 1; }
+    sc->beta = Gn / sc->G;
+    sc->G = Gn;
+  }
+  count_loop(sc);
+  set_loop_cond(use_cond, cond, sc);
 }
 
 // Detach every element of S with tensile stress -p > p_crit (Eq. 24).
@@ -1683,9 +1724,9 @@ void launch_box_scatter(const T* bp, T* p, int nx, int ny, int x0, int y0, int b
   k_box_scatter<T><<<ew_grid((size_t)nb), 256, 0, s>>>(bp, p, nx, ny, x0, y0, lbx, nb);
 }
 template <typename T>
-void launch_cg_update(const Plan& pl, Fields<T> f, double* part, Scalars* sc, int ngrid,
-                      cudaStream_t s) {
-  k_cg_update<T><<<ngrid, 256, 0, s>>>(pl.nx, f, part, sc);
+void launch_cg_update(const Plan& pl, Fields<T> f, double* part, Scalars* sc, int ngrid, int use_cond,
+                      unsigned long long cond, cudaStream_t s) {
+  k_cg_update<T><<<ngrid, 256, 0, s>>>(pl.nx, f, part, sc, use_cond, cond);
 }
 template <typename T>
 void launch_detach(const Plan& pl, Fields<T> f, double* part, Scalars* sc, int ngrid,
@@ -1735,8 +1776,8 @@ void launch_mask_field(T* x, const uint8_t* S, size_t n, cudaStream_t s) {
   template void launch_box_gather<T>(const T*, const T*, const uint8_t*, int, int, int, int, T*, T*, \
                                      uint8_t*, int, int, cudaStream_t);                         \
   template void launch_box_scatter<T>(const T*, T*, int, int, int, int, int, int, cudaStream_t); \
-  template void launch_cg_update<T>(const Plan&, Fields<T>, double*, Scalars*, int,            \
-                                    cudaStream_t);                                             \
+  template void launch_cg_update<T>(const Plan&, Fields<T>, double*, Scalars*, int, int,       \
+                                    unsigned long long, cudaStream_t);                         \
   template void launch_detach<T>(const Plan&, Fields<T>, double*, Scalars*, int, cudaStream_t); \
   template void launch_stats<T>(const Plan&, const T*, const T*, const uint8_t*, int, double*, \
                                 double*, int, cudaStream_t);                                   \

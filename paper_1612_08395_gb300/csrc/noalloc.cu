@@ -1,28 +1,29 @@
 // bem_convolve_noalloc: the FP64 stress -> displacement transform for callers
 // that may not allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a stream is being
-// captured into a CUDA graph (an allocation there breaks the capture), hosts
-// whose device memory is owned by a pool or arena the caller must not bypass,
+// Some callers cannot call cudaMalloc: hosts whose device memory is owned by a
+// caching allocator or arena that the library must not bypass (an allocation
+// beside such a pool fragments it, or fails once the pool holds the memory),
 // and latency-critical loops where cudaMalloc's implicit device-wide
 // synchronisation is not allowed.  This entry point allocates nothing: the
 // scratch the three transform passes need (the transposed half spectrum W, a
-// transposed copy of the kernel spectrum, the twiddle and index tables) lives in one file-scope device
-// array of kScratchBytes bytes, which every GPU that loads the library holds
-// until the process exits.
+// transposed copy of the kernel spectrum, the twiddle and index tables) lives
+// in one file-scope device array of kScratchBytes bytes, which every GPU that
+// loads the library holds until the process exits.
 //
 // The array's name in host code is only a host-side stand-in, not a device
 // address; its device address is obtained once per device with
 // cudaGetSymbolAddress (on the first call made with that device current) and
-// passed to the kernels.  Because that first call does this set-up, it should
-// come before any stream capture.
+// passed to the kernels.  That first call also opts the pass kernels into the
+// shared memory their launch shapes need (the same once-per-device set-up a
+// handle does), so it should come before any stream capture.
 //
 // Every call shares the array and it keeps the previous call's contents.
 // Nothing in it needs clearing: each call writes every element it later reads
 // (the spectrum copy, the twiddle and index tables and all of W) before
-// reading it.  Calls whose work
-// overlaps on the GPU (different streams, or different host threads) race on
-// the array and must be serialised by the caller.
+// reading it.  Calls whose work overlaps on the GPU (different streams, or
+// different host threads) race on the array and must be serialised by the
+// caller.
 #include <mutex>
 
 #include <cuda_runtime.h>
@@ -84,6 +85,10 @@ extern "C" int bem_convolve_noalloc(const double* khat, int Nx, int Ny, double c
   {
     std::lock_guard<std::mutex> lk(g_setup_mu);
     if (!g_scratch_dev[dev]) {
+      // once per device: the pass kernels' shared-memory opt-in, then the
+      // scratch array's device address
+      const int rc = bem::device_setup(dev);
+      if (rc != BEM_OK) return rc;
       void* ptr = nullptr;
       if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
         cudaGetLastError();
@@ -107,33 +112,14 @@ extern "C" int bem_convolve_noalloc(const double* khat, int Nx, int Ny, double c
   if (g_off + sizeof(int) * g_ints > kScratchBytes)
     return bem::set_error(BEM_EINVAL, "bem_convolve_noalloc: grid needs more than the 2 MiB static scratch");
 
-  // launch geometry of the plain FP64 passes (rows per CTA as a handle's plan
-  // chooses them before it spreads small grids over more CTAs)
-  bem::Plan pl{};
-  pl.nx = Nx; pl.ny = Ny; pl.px = px; pl.py = py; pl.M = M;
-  const int tr = M / 8;
-  int nb = 256 / tr;
-  if (nb < 2) nb = 2;
-  while (nb > 1 && nb * tr > 1024) nb >>= 1;
-  while (nb > 1 && (size_t)nb * (M + 32) * 16 > 128 * 1024) nb >>= 1;
-  pl.nbA = nb; pl.lognbA = ilog2i(nb);
-  pl.gA = bem::make_geo(ilog2i(M), nb, 8);
-  pl.threadsA = nb * tr; pl.gridA = (Ny + nb - 1) / nb;
-  pl.smemA = (size_t)nb * pl.gA.rs * 16; pl.smemC = pl.smemA;
-  const int tb = py / 8;
-  int nbb = 256 / tb;
-  if (nbb < 1) nbb = 1;
-  while (nbb > 1 && (size_t)nbb * (py + 32) * 16 > 128 * 1024) nbb >>= 1;
-  pl.nbB = nbb; pl.gB = bem::make_geo(ilog2i(py), nbb, 8);
-  pl.threadsB = nbb * tb; pl.gridB = (M + 1 + nbb - 1) / nbb;
-  pl.smemB = (size_t)nbb * pl.gB.rs * 16;
+  // launch geometry of the plain FP64 passes: the plan a handle of this grid
+  // uses for bem_convolve in FP64
   int nsm = 0;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
     return bem::set_error(BEM_ECUDA, "bem_convolve_noalloc: cannot query the SM count");
-  pl.nsm = nsm;  // the persistent row passes size their grids by it
-  // every pass stays within the default 48 KB of dynamic shared memory here
-  if (pl.smemA > 48 * 1024 || pl.smemB > 48 * 1024 || pl.smemC > 48 * 1024)
-    return bem::set_error(BEM_EINVAL, "bem_convolve_noalloc: grid too large for the default shared memory");
+  const bem::Plan pl = bem::default_plan(Nx, Ny, px, py, 8, nsm);
+  if (!bem::plan_fits(pl, 8))
+    return bem::set_error(BEM_EINVAL, "bem_convolve_noalloc: no launchable plan for this grid");
 
   cudaStream_t s = (cudaStream_t)stream;
   unsigned char* scratch = static_cast<unsigned char*>(base);

@@ -1,14 +1,20 @@
-// Request server: many independent contact solves in flight on one GPU.
+// Request server: many independent contact solves in flight on one or more GPUs.
 //
 // Worker threads (one CUDA stream each, through their handles) take jobs from
-// a queue.  A job is admitted when its device-memory footprint fits the HBM
-// budget next to the jobs already running and the cached handles; a job that
-// does not fit lets later, smaller jobs go first (continuous batching rather
-// than a plain FIFO), and idle cached handles are evicted least recently used
-// first to make room.  Handles are cached by (Nx, Ny, dx, dy, k): the influence
+// a shared queue; each worker belongs to one device.  A job is admitted on a
+// device when its device-memory footprint fits that device's HBM budget next
+// to the jobs already running there and the handles cached there; a job that
+// does not fit yet lets later, smaller jobs go first (continuous batching
+// rather than a plain FIFO), and idle cached handles are evicted least
+// recently used first to make room.  With several devices, the placement
+// policy (place_job) sends a job to a device with an idle worker where it
+// fits, preferring one that holds an idle cached handle for its spectrum,
+// then the one with the most budget left after it.  Devices never share
+// work: a solve runs wholly on its device (no collective, no peer memory).
+// Handles are cached per device by (Nx, Ny, dx, dy, k): the influence
 // spectrum depends only on these, and nu, E0, c0 enter through the scalar A,
-// which bem_set_material updates.  Each solve is deterministic and touches only
-// its own handle, so its result is the same alone and in any mix.
+// which bem_set_material updates.  Each solve is deterministic and touches
+// only its own handle, so its result is the same alone and in any mix.
 #include <math.h>
 
 #include <algorithm>
@@ -77,17 +83,23 @@ struct Pending {
   size_t need;
 };
 
+// One device's share of the server: its budget, cached handles and workers.
+struct DevPool {
+  int device = 0;
+  size_t budget = 0;
+  size_t used = 0;          // bytes of cached handles (busy or idle) + reservations
+  std::list<Cached> cache;  // front = most recently used
+  int workers = 0, busy = 0;
+};
+
 }  // namespace
 
 struct bem_server {
-  int device = 0;
-  size_t budget = 0;
   std::chrono::steady_clock::time_point t0;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<Pending> queue;
-  std::list<Cached> cache;  // front = most recently used
-  size_t used = 0;          // bytes of cached handles (busy or idle) + reservations
+  std::vector<DevPool> devs;
   int running = 0;
   bool stop = false;
   std::deque<bem_completion> done;
@@ -97,55 +109,79 @@ struct bem_server {
 namespace {
 
 // Find a cached idle handle for key (moved to the front) or nullptr.
-Cached* take_cached(bem_server* s, const Key& k) {
-  for (auto it = s->cache.begin(); it != s->cache.end(); ++it) {
+Cached* take_cached(DevPool& d, const Key& k) {
+  for (auto it = d.cache.begin(); it != d.cache.end(); ++it) {
     if (!it->busy && it->key == k) {
-      s->cache.splice(s->cache.begin(), s->cache, it);
-      s->cache.front().busy = true;
-      return &s->cache.front();
+      d.cache.splice(d.cache.begin(), d.cache, it);
+      d.cache.front().busy = true;
+      return &d.cache.front();
     }
   }
   return nullptr;
 }
 
 // Evict idle cached handles (least recently used first) until `need` bytes fit.
-bool make_room(bem_server* s, size_t need) {
-  while (s->used + need > s->budget) {
-    auto it = s->cache.end();
+bool make_room(DevPool& d, size_t need) {
+  while (d.used + need > d.budget) {
+    auto it = d.cache.end();
     bool found = false;
-    while (it != s->cache.begin()) {
+    while (it != d.cache.begin()) {
       --it;
       if (!it->busy) { found = true; break; }
     }
     if (!found) return false;
-    s->used -= it->bytes;
+    d.used -= it->bytes;
     bem_destroy(it->h);
-    s->cache.erase(it);
+    d.cache.erase(it);
   }
   return true;
 }
 
-void worker_main(bem_server* s) {
-  cudaSetDevice(s->device);
+// The placement view of every device for one job (see bem_device_view).
+void device_views(const bem_server* s, const Key& k, std::vector<bem_device_view>& v) {
+  v.resize(s->devs.size());
+  for (size_t i = 0; i < s->devs.size(); ++i) {
+    const DevPool& d = s->devs[i];
+    bem_device_view& w = v[i];
+    w.budget = d.budget;
+    w.used = d.used;
+    w.evictable = 0;
+    w.cached_bytes = 0;
+    w.has_cached = 0;
+    for (const Cached& c : d.cache) {
+      if (c.busy) continue;
+      if (!w.has_cached && c.key == k) { w.has_cached = 1; w.cached_bytes = c.bytes; }
+      else w.evictable += c.bytes;
+    }
+    w.idle_workers = d.workers - d.busy;
+  }
+}
+
+void worker_main(bem_server* s, int di) {
+  cudaSetDevice(s->devs[di].device);
+  std::vector<bem_device_view> views;
   for (;;) {
     Pending p;
     Cached* slot = nullptr;
     size_t reserved = 0;
     {
       std::unique_lock<std::mutex> lk(s->mu);
+      DevPool& dev = s->devs[di];
       for (;;) {
         if (s->stop && s->queue.empty()) return;
-        // first queued job that is cached or fits the budget (after evictions)
+        // the first queued job whose placement is this worker's device
         bool picked = false;
         for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
           const Key k{it->job.Nx, it->job.Ny, it->job.dx, it->job.dy, it->job.k};
-          if ((slot = take_cached(s, k)) != nullptr) {
+          device_views(s, k, views);
+          if (bem_server_place((int)views.size(), views.data(), it->need) != di) continue;
+          if ((slot = take_cached(dev, k)) != nullptr) {
             // room for the fields of a precision the cached handle has not used yet
             const size_t grow = it->need > slot->bytes ? it->need - slot->bytes : 0;
-            if (make_room(s, grow)) {
+            if (make_room(dev, grow)) {
               p = *it;
               reserved = grow;
-              s->used += reserved;
+              dev.used += reserved;
               s->queue.erase(it);
               picked = true;
               break;
@@ -153,10 +189,10 @@ void worker_main(bem_server* s) {
             slot->busy = false;
             slot = nullptr;
           }
-          if (make_room(s, it->need)) {
+          if (make_room(dev, it->need)) {
             p = *it;
             reserved = it->need;
-            s->used += reserved;
+            dev.used += reserved;
             s->queue.erase(it);
             picked = true;
             break;
@@ -165,10 +201,14 @@ void worker_main(bem_server* s) {
         if (picked) break;
         s->cv_work.wait(lk);
       }
+      dev.busy++;
       s->running++;
     }
+    // another device's worker may be the placement of the next queued job
+    s->cv_work.notify_all();
     bem_completion c{};
     c.tag = p.job.tag;
+    c.device = s->devs[di].device;
     c.t_submit = p.t_submit;
     c.t_start = now_s(s->t0);
     int rc = BEM_OK;
@@ -186,12 +226,13 @@ void worker_main(bem_server* s) {
     c.status = rc;
     {
       std::lock_guard<std::mutex> lk(s->mu);
-      s->used -= reserved;
+      DevPool& dev = s->devs[di];
+      dev.used -= reserved;
       if (slot) {
         // the job may have allocated the other precision's fields
         bem_info inf;
         if (bem_get_info(h, &inf) == BEM_OK && inf.device_bytes != slot->bytes) {
-          s->used = s->used - slot->bytes + inf.device_bytes;
+          dev.used = dev.used - slot->bytes + inf.device_bytes;
           slot->bytes = inf.device_bytes;
         }
         slot->busy = false;
@@ -201,15 +242,16 @@ void worker_main(bem_server* s) {
           size_t bytes = reserved;
           if (bem_get_info(h, &inf) == BEM_OK) bytes = inf.device_bytes;
           if (rc == BEM_OK || rc == BEM_ENOCONV) {
-            s->cache.push_front(Cached{Key{p.job.Nx, p.job.Ny, p.job.dx, p.job.dy, p.job.k}, h, bytes, false});
-            s->used += bytes;
+            dev.cache.push_front(Cached{Key{p.job.Nx, p.job.Ny, p.job.dx, p.job.dy, p.job.k}, h, bytes, false});
+            dev.used += bytes;
           } else {
             bem_destroy(h);
           }
         }
       }
       // keep the cache within the budget
-      make_room(s, 0);
+      make_room(dev, 0);
+      dev.busy--;
       s->running--;
       s->done.push_back(c);
     }
@@ -220,26 +262,76 @@ void worker_main(bem_server* s) {
 
 }  // namespace
 
+extern "C" int bem_server_place(int ndev, const bem_device_view* v, size_t need) {
+  if (ndev < 1 || !v) return -1;
+  int best = -1;
+  bool best_cached = false;
+  size_t best_left = 0;
+  for (int i = 0; i < ndev; ++i) {
+    if (v[i].idle_workers < 1) continue;
+    const bool cached = v[i].has_cached != 0;
+    const size_t here = cached ? (need > v[i].cached_bytes ? need - v[i].cached_bytes : 0) : need;
+    // bytes that stay held: running jobs' reservations and busy handles (idle
+    // cached handles other than the job's own can be evicted)
+    const size_t idle = v[i].evictable + (cached ? v[i].cached_bytes : 0);
+    const size_t pinned = v[i].used > idle ? v[i].used - idle : 0;
+    const size_t keep = pinned + (cached ? v[i].cached_bytes : 0);
+    if (keep + here > v[i].budget) continue;
+    const size_t left = v[i].budget - (keep + here);
+    if (best < 0 || (cached && !best_cached) || (cached == best_cached && left > best_left)) {
+      best = i;
+      best_cached = cached;
+      best_left = left;
+    }
+  }
+  return best;
+}
+
 extern "C" size_t bem_server_footprint(int Nx, int Ny) {
   if (Nx < 2 || Ny < 2 || Nx > 4096 || Ny > 4096) return 0;
   return footprint(Nx, Ny);
 }
 
+extern "C" int bem_server_create_on(int ndev, const int* devices, int workers_per_device,
+                                    size_t hbm_budget_per_device, bem_server_handle* out) {
+  if (!out || ndev < 1 || ndev > 64 || !devices || workers_per_device < 1 || workers_per_device > 64 ||
+      hbm_budget_per_device < ((size_t)64 << 20))
+    return bem::set_error(BEM_EINVAL, "bem_server_create_on: 1..64 devices, 1..64 workers each and a budget "
+                                      "of at least 64 MiB per device");
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || count < 1) {
+    cudaGetLastError();
+    return bem::set_error(BEM_ECUDA, "bem_server_create_on: no CUDA device");
+  }
+  for (int i = 0; i < ndev; ++i) {
+    if (devices[i] < 0 || devices[i] >= count)
+      return bem::set_error(BEM_EINVAL, "bem_server_create_on: device index out of range");
+    for (int j = 0; j < i; ++j)
+      if (devices[j] == devices[i]) return bem::set_error(BEM_EINVAL, "bem_server_create_on: repeated device");
+  }
+  bem_server* s = new bem_server();
+  s->t0 = std::chrono::steady_clock::now();
+  s->devs.resize(ndev);
+  for (int i = 0; i < ndev; ++i) {
+    s->devs[i].device = devices[i];
+    s->devs[i].budget = hbm_budget_per_device;
+    s->devs[i].workers = workers_per_device;
+  }
+  for (int i = 0; i < ndev; ++i)
+    for (int w = 0; w < workers_per_device; ++w) s->workers.emplace_back(worker_main, s, i);
+  *out = s;
+  return BEM_OK;
+}
+
 extern "C" int bem_server_create(int nworkers, size_t hbm_budget_bytes, bem_server_handle* out) {
   if (!out || nworkers < 1 || nworkers > 64 || hbm_budget_bytes < ((size_t)64 << 20))
     return bem::set_error(BEM_EINVAL, "bem_server_create: nworkers must be 1..64 and the budget at least 64 MiB");
-  int dev = 0, ndev = 0;
-  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1 || cudaGetDevice(&dev) != cudaSuccess) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
     return bem::set_error(BEM_ECUDA, "bem_server_create: no CUDA device");
   }
-  bem_server* s = new bem_server();
-  s->device = dev;
-  s->budget = hbm_budget_bytes;
-  s->t0 = std::chrono::steady_clock::now();
-  for (int i = 0; i < nworkers; ++i) s->workers.emplace_back(worker_main, s);
-  *out = s;
-  return BEM_OK;
+  return bem_server_create_on(1, &dev, nworkers, hbm_budget_bytes, out);
 }
 
 extern "C" int bem_server_submit(bem_server_handle s, const bem_job* job) {
@@ -250,9 +342,11 @@ extern "C" int bem_server_submit(bem_server_handle s, const bem_job* job) {
   const size_t need = footprint(job->Nx, job->Ny);
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->stop) return bem::set_error(BEM_EINVAL, "bem_server_submit: server is shutting down");
-  if (need > s->budget) return bem::set_error(BEM_ENOMEM, "bem_server_submit: job footprint exceeds the budget");
+  size_t largest = 0;
+  for (const DevPool& d : s->devs) largest = d.budget > largest ? d.budget : largest;
+  if (need > largest) return bem::set_error(BEM_ENOMEM, "bem_server_submit: job footprint exceeds the budget");
   s->queue.push_back(Pending{*job, now_s(s->t0), need});
-  s->cv_work.notify_one();
+  s->cv_work.notify_all();
   return BEM_OK;
 }
 
@@ -278,6 +372,7 @@ extern "C" int bem_server_cancel(bem_server_handle s, long long tag) {
       bem_completion c{};
       c.tag = tag;
       c.status = BEM_ECANCELED;
+      c.device = -1;
       c.t_submit = it->t_submit;
       c.t_start = c.t_end = now_s(s->t0);
       s->queue.erase(it);
@@ -298,7 +393,9 @@ extern "C" int bem_server_pending(bem_server_handle s) {
 extern "C" size_t bem_server_bytes(bem_server_handle s) {
   if (!s) return 0;
   std::lock_guard<std::mutex> lk(s->mu);
-  return s->used;
+  size_t b = 0;
+  for (const DevPool& d : s->devs) b += d.used;
+  return b;
 }
 
 extern "C" void bem_server_destroy(bem_server_handle s) {
@@ -309,6 +406,12 @@ extern "C" void bem_server_destroy(bem_server_handle s) {
   }
   s->cv_work.notify_all();
   for (auto& t : s->workers) t.join();
-  for (auto& c : s->cache) bem_destroy(c.h);
+  int prev = 0;
+  const bool have_prev = cudaGetDevice(&prev) == cudaSuccess;
+  for (DevPool& d : s->devs) {
+    cudaSetDevice(d.device);
+    for (auto& c : d.cache) bem_destroy(c.h);
+  }
+  if (have_prev) cudaSetDevice(prev);
   delete s;
 }

@@ -75,7 +75,12 @@ namespace {
 #ifndef BEM_CHUNK
 #define BEM_CHUNK 8
 #endif
-constexpr int kChunk = BEM_CHUNK;  // CG iterations per captured graph launch
+constexpr int kChunk = BEM_CHUNK;  // CG iterations of the timed (event-recording) chunk graph
+// CG iterations per body of the device-driven while-loop graph
+#ifndef BEM_LOOP_BODY
+#define BEM_LOOP_BODY 4
+#endif
+constexpr int kLoopBody = BEM_LOOP_BODY;
 
 // Threads per CTA of the row passes (rows per CTA x M/8); 512 keeps two CTAs
 // resident per SM at the passes' register use.
@@ -86,7 +91,9 @@ constexpr int kChunk = BEM_CHUNK;  // CG iterations per captured graph launch
 template <typename T> struct PrecFields {
   T *p = nullptr, *g = nullptr, *t = nullptr, *r = nullptr, *c = nullptr;
   bool ready = false;
-  cudaGraphExec_t pk_graph[2] = {nullptr, nullptr}, cg_graph[2] = {nullptr, nullptr};  // [timed]
+  // [0]: the device-driven loop (while node), [1]: a chunk of kChunk iterations
+  // with event records around the passes of its first iteration (pass timing)
+  cudaGraphExec_t pk_graph[2] = {nullptr, nullptr}, cg_graph[2] = {nullptr, nullptr};
 };
 
 int ilog2(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
@@ -157,6 +164,34 @@ Plan make_plan(int nx, int ny, int px, int py, int esize, int nsm) {
 }
 
 }  // namespace
+
+namespace bem {
+Plan default_plan(int nx, int ny, int px, int py, int esize, int nsm) {
+  return make_plan(nx, ny, px, py, esize, nsm);
+}
+bool plan_fits(const Plan& pl, int esize) { return shape_fits(pl, esize); }
+
+// Once per device and process, with that device current: opt every pass kernel
+// into the shared memory it may ask for, and upload the quadrature nodes.
+int device_setup(int dev) {
+  static std::mutex init_mu;
+  static bool init_done[64] = {};
+  std::lock_guard<std::mutex> lk(init_mu);
+  if (dev < 0 || dev >= 64) return fail(BEM_ECUDA, "device index %d unsupported", dev);
+  if (init_done[dev]) return BEM_OK;
+  const int smem_max = 227 * 1024;
+  cudaError_t ea = set_smem_attrs_a<float>(smem_max);
+  if (ea == cudaSuccess) ea = set_smem_attrs_b<float>(smem_max);
+  if (ea == cudaSuccess) ea = set_smem_attrs_c<float>(smem_max);
+  if (ea == cudaSuccess) ea = set_smem_attrs_a<double>(smem_max);
+  if (ea == cudaSuccess) ea = set_smem_attrs_b<double>(smem_max);
+  if (ea == cudaSuccess) ea = set_smem_attrs_c<double>(smem_max);
+  if (ea != cudaSuccess) return fail(BEM_ECUDA, "shared-memory opt-in failed: %s", cudaGetErrorString(ea));
+  if (influence_init_nodes() != 0) return fail(BEM_ECUDA, "quadrature nodes upload failed");
+  init_done[dev] = true;
+  return BEM_OK;
+}
+}  // namespace bem
 
 struct bem_ctx {
   int device = 0;
@@ -298,6 +333,10 @@ int download(bem_ctx* h, double* dst, const double* src, size_t n) {
 
 int device_error(bem_ctx* h) {
   const unsigned e = h->sc_host->kerr;
+  // reported once: clear the word so the next solve on this handle starts clean
+  h->sc_host->kerr = 0;
+  cudaMemsetAsync(&h->sc->kerr, 0, sizeof(unsigned), h->stream);
+  cudaStreamSynchronize(h->stream);
   if (e & 2u) return fail(BEM_ECUDA, "a debug bounds check failed in a kernel (error bits %#x)", e);
   return fail(BEM_ETIMEOUT, "a kernel gave up waiting for its own asynchronous copies (error bits %#x)", e);
 }
@@ -317,11 +356,18 @@ int init_scalars(bem_ctx* h, double tol, int max_iter, double pcrit) {
   s.delta = 0.0;
   s.bnorm = 1.0;
   s.pcrit = pcrit;
+  s.max_loops = max_iter + 64;  // the device-driven loop's bound
   s.band0 = h->ny;  // empty box until k_box runs
   s.band1 = -1;
   s.col0 = h->nx;
   s.col1 = -1;
   s.kerr = h->sc_host->kerr;
+#ifdef BEM_DEBUG_CHECKS
+  // test hook: BEM_INJECT_WAIT_TIMEOUT=1 makes the solve's first persistent
+  // pass A launch run a bounded wait out (reported as BEM_ETIMEOUT)
+  const char* inj = getenv("BEM_INJECT_WAIT_TIMEOUT");
+  s.inject = inj && inj[0] == '1';
+#endif
   *h->sc_host = s;
   // every member but the sticky error word
   CK(cudaMemcpyAsync(h->sc, h->sc_host, offsetof(Scalars, kerr), cudaMemcpyHostToDevice, h->stream));
@@ -343,31 +389,27 @@ void conv_plain(bem_ctx* h, const T* x, T* dst, cudaStream_t s) {
   h->launches += 3;
 }
 
+// A launch failed while capturing: report it (the caller ends the capture).
 #define CAPTURE_CHECK(what)                                                                  \
   do {                                                                                       \
     cudaError_t le_ = cudaPeekAtLastError();                                                 \
     if (le_ != cudaSuccess) {                                                                \
-      cudaGraph_t g_;                                                                        \
-      cudaStreamEndCapture(h->stream, &g_);                                                  \
-      if (g_) cudaGraphDestroy(g_);                                                          \
       cudaGetLastError();                                                                    \
       return fail(BEM_ECUDA, "capture: %s failed: %s", what, cudaGetErrorString(le_));      \
     }                                                                                        \
   } while (0)
 
+// The passes of `iters` CG iterations, captured on the handle's stream; with
+// `ev`, event records around the three passes of the first iteration.
 template <typename T>
-int capture(bem_ctx* h, bool pk, bool timed, cudaGraphExec_t* out) {
-  cudaGraph_t graph;
-  cudaEvent_t* ev = h->ev[pk ? 0 : 1];
-  if (timed && !ev[0])
-    for (int i = 0; i < 4; ++i) CK(cudaEventCreate(&ev[i]));
-  CK(cudaGetLastError());
-  CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+int capture_iterations(bem_ctx* h, bool pk, int iters, cudaEvent_t* ev, int use_cond, unsigned long long cond) {
   PassArgs<T> a = make_args<T>(h);
   a.use_band = pk ? 0 : 1;  // fixed-set CG: only the contact band's rows
+  a.use_cond = use_cond;
+  a.cond = cond;
   Fields<T> f = a.f;
-  for (int it = 0; it < kChunk; ++it) {
-    const bool mark = timed && it == 0;
+  for (int it = 0; it < iters; ++it) {
+    const bool mark = ev && it == 0;
     if (mark) cudaEventRecordWithFlags(ev[0], h->stream, cudaEventRecordExternal);
     CAPTURE_CHECK("event 0");
     launch_pass_a<T>(a, pk ? A_PK_P : A_CG_T, h->stream);
@@ -388,15 +430,73 @@ int capture(bem_ctx* h, bool pk, bool timed, cudaGraphExec_t* out) {
       launch_pass_c<T>(a, C_PK_R, h->stream);
       CAPTURE_CHECK("pass C (t)");
     } else {
-      launch_cg_update<T>(a.pl, f, h->partE, h->sc, h->ew_ngrid, h->stream);
+      launch_cg_update<T>(a.pl, f, h->partE, h->sc, h->ew_ngrid, use_cond, cond, h->stream);
       CAPTURE_CHECK("cg update");
     }
   }
+  return BEM_OK;
+}
+
+// Timed chunk: kChunk iterations with event records (BEM_FLAG_TIME_PASSES).
+template <typename T>
+int capture_timed(bem_ctx* h, bool pk, cudaGraphExec_t* out) {
+  cudaGraph_t graph;
+  cudaEvent_t* ev = h->ev[pk ? 0 : 1];
+  if (!ev[0])
+    for (int i = 0; i < 4; ++i) CK(cudaEventCreate(&ev[i]));
+  CK(cudaGetLastError());
+  CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  const int rc = capture_iterations<T>(h, pk, kChunk, ev, 0, 0);
+  graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
-  if (e != cudaSuccess) return fail(BEM_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+  if (rc != BEM_OK || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc != BEM_OK ? rc : fail(BEM_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+  }
   e = cudaGraphInstantiate(out, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return fail(BEM_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+  return BEM_OK;
+}
+
+// The device-driven CG loop: one graph whose while node repeats a body of
+// kLoopBody iterations until the kernel that finishes an iteration's scalars
+// clears the condition (the solve is done: converged, capped or failed).  One
+// launch runs the whole solve; the host reads the scalars once, at the end.
+template <typename T>
+int capture_loop(bem_ctx* h, bool pk, cudaGraphExec_t* out) {
+  cudaGraph_t graph = nullptr;
+  CK(cudaGetLastError());
+  CK(cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle cond;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = cond;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return fail(BEM_ECUDA, "while-loop graph set-up failed: %s", cudaGetErrorString(e));
+  }
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  e = cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return fail(BEM_ECUDA, "loop body capture failed: %s", cudaGetErrorString(e));
+  }
+  int rc = capture_iterations<T>(h, pk, kLoopBody, nullptr, 1, (unsigned long long)cond);
+  cudaGraph_t body_out = nullptr;
+  e = cudaStreamEndCapture(h->stream, &body_out);
+  if (rc != BEM_OK || e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return rc != BEM_OK ? rc : fail(BEM_ECUDA, "loop body capture failed: %s", cudaGetErrorString(e));
+  }
+  e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(BEM_ECUDA, "loop graph instantiate failed: %s", cudaGetErrorString(e));
   return BEM_OK;
 }
 
@@ -418,36 +518,37 @@ void add_pass_work(bem_ctx* h, bool pk, int rows, int es) {
   h->pass_flops[2] += rows * (0.5 * fm + 20 * M);
 }
 
-// Under BEM_FLAG_TIME_PASSES every kTimeEvery-th chunk (the first of each
-// solve included) runs the graph with event-record nodes; the others run the
-// plain graph, so the sampling costs little of the time it measures.
-constexpr int kTimeEvery = 4;
-
-int run_loop(bem_ctx* h, cudaGraphExec_t g, cudaGraphExec_t g_timed, int max_iter, bool pk, int es) {
-  const int max_launch = max_iter / kChunk + 2;
-  for (int l = 0; l < max_launch; ++l) {
-    const bool timed = h->timing && l % kTimeEvery == 0;
-    CK(cudaGraphLaunch(timed ? g_timed : g, h->stream));
-    h->launches += (unsigned long long)kChunk * (pk ? 6 : 4);
+// Run the solve's CG loop until the device sets `done`: under
+// BEM_FLAG_TIME_PASSES first one timed chunk (its passes' durations and work
+// are accumulated), then the device-driven loop graph.
+int run_loop(bem_ctx* h, cudaGraphExec_t g_loop, cudaGraphExec_t g_timed, bool pk, int es) {
+  const int kpi = pk ? 6 : 4;  // kernels per iteration
+  if (h->timing) {
+    CK(cudaGraphLaunch(g_timed, h->stream));
+    h->launches += (unsigned long long)kChunk * kpi;
     CKR(read_scalars(h));
-    if (timed) {
-      cudaEvent_t* ev = h->ev[pk ? 0 : 1];
-      for (int i = 0; i < 3; ++i) {
-        float ms = 0;
-        CK(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
-        h->pass_ms[i] += ms;
-      }
-      h->pass_count[0] += 1;
-      int rows = h->ny;
-      if (!pk) {
-        h->pass_count[1] += 1;
-        const int b0 = h->sc_host->band0, b1 = h->sc_host->band1;
-        rows = b1 >= b0 ? b1 - b0 + 1 : 0;
-      }
-      add_pass_work(h, pk, rows, es);
+    cudaEvent_t* ev = h->ev[pk ? 0 : 1];
+    for (int i = 0; i < 3; ++i) {
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
+      h->pass_ms[i] += ms;
     }
+    h->pass_count[0] += 1;
+    int rows = h->ny;
+    if (!pk) {
+      h->pass_count[1] += 1;
+      const int b0 = h->sc_host->band0, b1 = h->sc_host->band1;
+      rows = b1 >= b0 ? b1 - b0 + 1 : 0;
+    }
+    add_pass_work(h, pk, rows, es);
     if (h->sc_host->done) return BEM_OK;
   }
+  const int loops0 = h->sc_host->loops;
+  CK(cudaGraphLaunch(g_loop, h->stream));
+  CKR(read_scalars(h));
+  const int ran = h->sc_host->loops - loops0 + 1;  // iterations started in the loop graph
+  h->launches += (unsigned long long)((ran + kLoopBody - 1) / kLoopBody) * kLoopBody * kpi;
+  if (!h->sc_host->done) return fail(BEM_ECUDA, "the device-driven CG loop stopped before the solve was done");
   return BEM_OK;
 }
 
@@ -455,10 +556,12 @@ struct StepOut {
   int iterations = 0;
   double eps = 0;
   int status = BEM_OK;
+  int stalls = 0;  // CG solves that ended on the stall guard above their tolerance
 };
 
 // SC_STALL (eps stopped falling: the arithmetic's rounding floor) counts as
-// converged; final_eps reports where it stopped.
+// converged; final_eps reports where it stopped and the result counts it in
+// `stalled`.
 int map_status(int sc_status) {
   if (sc_status == SC_NOCONV) return BEM_ENOCONV;
   if (sc_status == SC_NUMERIC) return BEM_ENUMERIC;
@@ -483,15 +586,16 @@ int run_pk(bem_ctx* h, double d, double tol, int max_iter, bool warm, StepOut* s
     CKR(pick_sub(h, &sub));
     if (sub) return pk_in_box<T>(h, sub, d, tol, max_iter, warm, so);
   }
-  if (!pf.pk_graph[0]) CKR(capture<T>(h, true, false, &pf.pk_graph[0]));
-  if (h->timing && !pf.pk_graph[1]) CKR(capture<T>(h, true, true, &pf.pk_graph[1]));
+  if (!pf.pk_graph[0]) CKR(capture_loop<T>(h, true, &pf.pk_graph[0]));
+  if (h->timing && !pf.pk_graph[1]) CKR(capture_timed<T>(h, true, &pf.pk_graph[1]));
   launch_pk_init<T>(plan_of<T>(h), h->h64, d, pf.c, pf.p, pf.t, warm ? 1 : 0, h->ew_ngrid, h->stream);
   h->launches += 1;
   CKR(init_scalars(h, tol, max_iter, 0.0));
-  CKR(run_loop(h, pf.pk_graph[0], pf.pk_graph[1], max_iter, true, (int)sizeof(T)));
+  CKR(run_loop(h, pf.pk_graph[0], pf.pk_graph[1], true, (int)sizeof(T)));
   so->iterations += h->sc_host->iter;
   so->eps = h->sc_host->eps;
   if (h->sc_host->status != SC_OK) so->status = map_status(h->sc_host->status);
+  if (h->sc_host->status == SC_STALL) so->stalls += 1;
   return BEM_OK;
 }
 
@@ -588,6 +692,7 @@ int pk_in_box(bem_ctx* h, bem_ctx* sub, double d, double tol, int max_iter, bool
   absorb_sub(h, sub);
   so->iterations += bo.iterations;
   so->eps = bo.eps;
+  so->stalls += bo.stalls;
   if (bo.status != BEM_OK) so->status = bo.status;
   return BEM_OK;
 }
@@ -613,6 +718,7 @@ int fixed_cg_in_box(bem_ctx* h, bem_ctx* sub, double tol, int max_iter, double p
   absorb_sub(h, sub);
   so->iterations += bo.iterations;
   so->eps = bo.eps;
+  so->stalls += bo.stalls;
   if (bo.status != BEM_OK) so->status = bo.status;
   return BEM_OK;
 }
@@ -631,8 +737,8 @@ int run_fixed_cg(bem_ctx* h, double tol, int max_iter, double pcrit, StepOut* so
     CKR(pick_sub(h, &sub));
     if (sub) return fixed_cg_in_box<T>(h, sub, tol, max_iter, pcrit, so);
   }
-  if (!pf.cg_graph[0]) CKR(capture<T>(h, false, false, &pf.cg_graph[0]));
-  if (h->timing && !pf.cg_graph[1]) CKR(capture<T>(h, false, true, &pf.cg_graph[1]));
+  if (!pf.cg_graph[0]) CKR(capture_loop<T>(h, false, &pf.cg_graph[0]));
+  if (h->timing && !pf.cg_graph[1]) CKR(capture_timed<T>(h, false, &pf.cg_graph[1]));
   const size_t n = (size_t)h->nx * h->ny;
   launch_mask_field<T>(pf.p, h->S, n, h->stream);
   launch_mask_field<T>(pf.t, h->S, n, h->stream);
@@ -643,10 +749,11 @@ int run_fixed_cg(bem_ctx* h, double tol, int max_iter, double pcrit, StepOut* so
   launch_pass_c<T>(a, C_CG_G, h->stream);
   h->launches += 5;
   CKR(read_scalars(h));
-  if (!h->sc_host->done) CKR(run_loop(h, pf.cg_graph[0], pf.cg_graph[1], max_iter, false, (int)sizeof(T)));
+  if (!h->sc_host->done) CKR(run_loop(h, pf.cg_graph[0], pf.cg_graph[1], false, (int)sizeof(T)));
   so->iterations += h->sc_host->iter;
   so->eps = h->sc_host->eps;
   if (h->sc_host->status != SC_OK) so->status = map_status(h->sc_host->status);
+  if (h->sc_host->status == SC_STALL) so->stalls += 1;
   return BEM_OK;
 }
 
@@ -730,6 +837,7 @@ int refine_here(bem_ctx* h, double d, bool adhesive, int sweeps, double tol64, d
     StepOut cg;
     CKR(run_fixed_cg<float>(h, tol32, 2000, 0.0, &cg));
     so->iterations += cg.iterations;
+    so->stalls += cg.stalls;
     if (h->sc_host->status == SC_NUMERIC) { so->status = BEM_ENUMERIC; break; }
     launch_refine_apply(h->io64, h->f32.p, res, h->S, adhesive ? 0 : 1, n, h->stream);
     h->launches += 1;
@@ -913,25 +1021,8 @@ static int create_ctx(int Nx, int Ny, double dx, double dy, double k, double nu,
     return cleanup(fail(BEM_ECUDA, "stream creation failed"));
   }
   {
-    // once per device and process: shared-memory opt-ins and quadrature nodes
-    static std::mutex init_mu;
-    static bool init_done[64] = {};
-    std::lock_guard<std::mutex> lk(init_mu);
-    if (h->device < 0 || h->device >= 64) return cleanup(fail(BEM_ECUDA, "device index %d unsupported", h->device));
-    if (!init_done[h->device]) {
-      // every kernel may use as much dynamic shared memory as the SM allows
-      const int smem_max = 227 * 1024;
-      cudaError_t ea = set_smem_attrs_a<float>(smem_max);
-      if (ea == cudaSuccess) ea = set_smem_attrs_b<float>(smem_max);
-      if (ea == cudaSuccess) ea = set_smem_attrs_c<float>(smem_max);
-      if (ea == cudaSuccess) ea = set_smem_attrs_a<double>(smem_max);
-      if (ea == cudaSuccess) ea = set_smem_attrs_b<double>(smem_max);
-      if (ea == cudaSuccess) ea = set_smem_attrs_c<double>(smem_max);
-      if (ea != cudaSuccess)
-        return cleanup(fail(BEM_ECUDA, "shared-memory opt-in failed: %s", cudaGetErrorString(ea)));
-      if (influence_init_nodes() != 0) return cleanup(fail(BEM_ECUDA, "quadrature nodes upload failed"));
-      init_done[h->device] = true;
-    }
+    const int rc0 = device_setup(h->device);
+    if (rc0 != BEM_OK) return cleanup(rc0);
   }
   h->nx = Nx; h->ny = Ny; h->dx = dx; h->dy = dy; h->k = k; h->nu = nu; h->E0 = E0; h->c0 = c0;
   h->alpha = alpha;
@@ -1212,6 +1303,7 @@ int step_nonadhesive(bem_ctx* h, const SolveCfg& cfg, double d, bool warm, bem_r
   r->final_eps = so.eps;
   r->detach_rounds = 0;
   r->status = so.status;
+  r->stalled = so.stalls;
   r->depth = d;
   return BEM_OK;
 }
@@ -1261,6 +1353,7 @@ int step_adhesive_t(bem_ctx* h, const SolveCfg& cfg, double d, double pcrit, bem
   r->final_eps = so.eps;
   r->detach_rounds = rounds;
   r->status = so.status;
+  r->stalled = so.stalls;
   r->depth = d;
   return BEM_OK;
 }

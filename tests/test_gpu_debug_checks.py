@@ -72,3 +72,46 @@ def test_debug_build_checks_pass_and_match_release(cuda_ok, tmp_path):
     for prec in ("fp64", "fp32_refine"):
         a, b = np.array(dbg["rect_" + prec][3]), np.array(rel["rect_" + prec][3])
         assert np.linalg.norm(a - b) <= 1e-9 * max(np.linalg.norm(b), 1e-300)
+
+
+TIMEOUT_CASE = r"""
+import json, os, sys, time
+sys.path.insert(0, %r)
+from paper_1612_08395_gb300 import build
+build.build(debug_checks=True)
+import paper_1612_08395_gb300.bem as bem
+import paper_1612_08395_gb300.inputs as I
+n = 64
+prof = I.paraboloid(n)
+out = {}
+with bem.Handle(n, n, 1.0 / n, 1.0 / n, 0.5, 0.3) as h:
+    r0, rc0 = h.solve(prof, 0.01, precision="fp32")
+    os.environ["BEM_INJECT_WAIT_TIMEOUT"] = "1"
+    t0 = time.time()
+    r1, rc1 = h.solve(prof, 0.01, precision="fp32", check=False)
+    out["wait_s"] = time.time() - t0
+    out["msg"] = bem.load_library().bem_last_error().decode()
+    del os.environ["BEM_INJECT_WAIT_TIMEOUT"]
+    r2, rc2 = h.solve(prof, 0.01, precision="fp32")
+out["rc"] = [rc0, rc1, rc2]
+out["force"] = [r0.force, r2.force]
+out["count"] = [r0.contact_count, r2.contact_count]
+print(json.dumps(out))
+"""
+
+
+def test_bounded_wait_runs_out_and_handle_recovers(cuda_ok, tmp_path):
+    """A persistent pass waits (bounded) on a barrier that nothing completes --
+    a debug-build test hook, after every copy the pass issued has landed.  The
+    wait runs out, the kernel gives up and the solve returns BEM_ETIMEOUT; the
+    next solve on the same handle gives the clean solve's result."""
+    env = dict(os.environ, BEM_DEBUG_CHECKS="1")
+    env.pop("BEM_INJECT_WAIT_TIMEOUT", None)
+    r = subprocess.run([sys.executable, "-c", TIMEOUT_CASE % ROOT], capture_output=True, text=True,
+                       env=env, timeout=600, cwd=str(tmp_path))
+    assert r.returncode == 0, r.stderr[-3000:]
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    assert out["rc"] == [0, -5, 0], out
+    assert "gave up waiting" in out["msg"]
+    assert out["wait_s"] < 30.0
+    assert out["force"][0] == out["force"][1] and out["count"][0] == out["count"][1]

@@ -10,7 +10,47 @@ import paper_1612_08395_gb300.inputs as I
 pytestmark = pytest.mark.gpu
 
 FIELDS = ("force", "area", "contact_radius", "final_eps", "max_gap_violation", "depth",
-          "iterations", "detach_rounds", "contact_count", "status")
+          "iterations", "detach_rounds", "contact_count", "status", "stalled")
+
+# pressure tolerance of each precision mode against the FP64 oracle at the
+# default solver tolerances (plain FP32: the rounding floor of its transform
+# times the conditioning; the others: the FP64 stopping rules)
+MODE_TOL = {"fp64": 1e-8, "fp32_refine": 1e-8, "fp32": 5e-4}
+
+
+def oracle_job(oracle_mod, job):
+    """The oracle's result for a job: per-step contact counts and the final pressure
+    (non-adhesive: Polonsky-Keer at the depth; adhesive: preload, then the held-set
+    solve and detach loop at each unloading depth, Sec. 3.1)."""
+    n = job["n"]
+    dx = 1.0 / n
+    h, ds = I.job_profile(job)
+    A = oracle_mod.compliance(job["k"], job["nu"])
+    conv = oracle_mod.FFTConvolver(oracle_mod.influence_quarter(job["k"], dx, dx, n + 1, n + 1), n, n)
+    if job["dgamma"] > 0:
+        out, p, S = oracle_mod.adhesive_unload(A, conv, h, ds[0], ds[1:],
+                                               oracle_mod.p_crit(job["k"], job["nu"], job["dgamma"], dx),
+                                               dx * dx, tol_pk=1e-12, tol_cg=1e-13)
+        pre = oracle_mod.pk_solve(A, conv, h, ds[0], tol=1e-12)
+        return [int((pre.p > 0).sum())] + [o["count"] for o in out], p
+    res = oracle_mod.pk_solve(A, conv, h, ds[0], tol=1e-12)
+    return [int((res.p > 0).sum())], res.p
+
+
+def assert_matches_oracle(oracle_mod, job, results, p):
+    counts, p_ref = oracle_job(oracle_mod, job)
+    tol = MODE_TOL[job["precision"]]
+    got = [r["contact_count"] if isinstance(r, dict) else r.contact_count for r in results]
+    if job["precision"] == "fp32":
+        # plain FP32 may round an element at the contact edge to the other side
+        assert all(abs(a - b) <= max(2, 0.002 * b) for a, b in zip(got, counts)), (got, counts)
+    else:
+        assert got == counts, (job, got, counts)
+    nrm = np.linalg.norm(p_ref)
+    if nrm > 0:
+        assert np.linalg.norm(p - p_ref) <= tol * nrm, (job, np.linalg.norm(p - p_ref) / nrm)
+    else:
+        assert np.abs(p).max() == 0
 
 
 def small_jobs():
@@ -59,7 +99,7 @@ def assert_same(alone, comp):
     assert np.array_equal(p_a, comp["final_pressure"])
 
 
-def test_alone_equals_mix(bem_mod):
+def test_alone_equals_mix(bem_mod, oracle_mod):
     jobs = small_jobs()
     alone = [run_alone(bem_mod, j) for j in jobs]
     with bem_mod.Server(nworkers=4, hbm_budget_bytes=4 << 30) as srv:
@@ -67,8 +107,11 @@ def test_alone_equals_mix(bem_mod):
         comps = {c["tag"]: c for c in srv.drain()}
         assert srv.pending() == 0
     assert sorted(comps) == sorted(tags)
-    for t, a in zip(tags, alone):
+    for t, a, j in zip(tags, alone, jobs):
         assert_same(a, comps[t])
+        assert comps[t]["device"] >= 0
+        # and each served result is the oracle's, within its precision's tolerance
+        assert_matches_oracle(oracle_mod, j, comps[t]["results"], comps[t]["final_pressure"])
     # several jobs overlapped on the device
     iv = sorted((c["t_start"], c["t_end"]) for c in comps.values())
     assert any(iv[i + 1][0] < iv[i][1] for i in range(len(iv) - 1))
@@ -119,9 +162,11 @@ def test_failing_job_reports_status(bem_mod):
     assert comps[t_good]["status"] == bem_mod.BEM_OK
 
 
-def test_batch_fp32_refine_matches_fp64(bem_mod):
+def test_batch_fp32_refine_matches_fp64(bem_mod, oracle_mod):
     """Jobs of the batched mix (grid sides 128 and 256 here) at FP32 + refinement
-    agree with the FP64 path: pressure relative L2 <= 1e-5 and equal contact counts."""
+    agree with the FP64 path: pressure relative L2 <= 1e-5 and equal contact counts;
+    the 128^2 jobs also match the oracle (contact counts at every step exact,
+    final pressure within 1e-8 relative L2)."""
     jobs = [j for j in I.batch_jobs(48, seed=4, sides=(128, 256))][:12]
     with bem_mod.Server(nworkers=4, hbm_budget_bytes=8 << 30) as srv:
         t32 = [submit(srv, dict(j, precision="fp32_refine")) for j in jobs]
@@ -135,6 +180,13 @@ def test_batch_fp32_refine_matches_fp64(bem_mod):
         if nrm > 0:
             assert np.linalg.norm(pa - pb) <= 1e-5 * nrm
         assert ca["results"][-1].contact_count == cb["results"][-1].contact_count
+    checked = 0
+    for j, a in zip(jobs, t32):
+        if j["n"] == 128:
+            assert_matches_oracle(oracle_mod, dict(j, precision="fp32_refine"), comps[a]["results"],
+                                  comps[a]["final_pressure"])
+            checked += 1
+    assert checked >= 3
 
 
 def test_cancel_a_queued_job(bem_mod):
