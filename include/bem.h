@@ -48,9 +48,8 @@ extern "C" {
 #define BEM_PREC_FP32_REFINE 2
 
 /* Record CUDA events around the three transform passes of the first CG
- * iteration of every CG solve: each solve then starts with a captured chunk of
- * 8 iterations carrying the event records before its device-driven loop
- * continues (read back with bem_pass_times). */
+ * iteration of every fourth captured chunk of 8 iterations, the first chunk of
+ * every solve included (read back with bem_pass_times). */
 #define BEM_FLAG_TIME_PASSES 1
 
 typedef struct bem_ctx *bem_handle;
@@ -177,6 +176,16 @@ int bem_contact_set(bem_handle h, unsigned char *S_out);
  *   finished or unknown).
  * bem_server_pending: jobs queued or running.
  * bem_server_bytes: device bytes accounted to cached and running handles.
+ * bem_server_loop_stats: CG-loop batching so far.  Jobs running at the same
+ *   time on one device share their CG loops: when a job's solve reaches its
+ *   loop it joins the loops waiting at that moment (all jobs in flight, or
+ *   those that arrived within 200 us), and the loops of one size class (grid,
+ *   torus, launch shapes, precision and loop kind) run as one while-loop graph
+ *   in which every transform pass is a single launch over all of them, each
+ *   instance stopping at its own convergence (its CTAs return at once when it
+ *   is done).  *launches = such graphs launched, *loops = the solves' loops they
+ *   carried.  Results are bitwise those of the job run alone.
+ *   BEM_BATCH_LOOPS=0 in the environment makes every job run its own loops.
  * bem_server_footprint: the bytes admission reserves for a job on an Nx x Ny
  *   grid (a handle after FP32 and FP64 solves plus its set-up workspace);
  *   0 for a grid outside 2..4096.
@@ -233,6 +242,7 @@ int bem_server_poll(bem_server_handle s, bem_completion *out, int max, int wait_
 int bem_server_cancel(bem_server_handle s, long long tag);
 int bem_server_pending(bem_server_handle s);
 size_t bem_server_bytes(bem_server_handle s);
+int bem_server_loop_stats(bem_server_handle s, long long *launches, long long *loops);
 size_t bem_server_footprint(int Nx, int Ny);
 void bem_server_destroy(bem_server_handle s);
 

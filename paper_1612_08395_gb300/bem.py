@@ -132,6 +132,7 @@ def load_library(path: str = LIB_PATH):
     lib.bem_server_poll.argtypes = [vp, ctypes.POINTER(Completion), ip, ip]
     lib.bem_server_pending.argtypes = [vp]
     lib.bem_server_cancel.argtypes = [vp, ctypes.c_longlong]
+    lib.bem_server_loop_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     lib.bem_server_bytes.argtypes = [vp]
     lib.bem_server_bytes.restype = ctypes.c_size_t
     lib.bem_server_footprint.argtypes = [ip, ip]
@@ -375,6 +376,12 @@ class Server:
 
     def device_bytes(self):
         return load_library().bem_server_bytes(self._s)
+
+    def loop_stats(self):
+        """(batched loop graphs launched, solves' CG loops they carried)."""
+        a, b = ctypes.c_longlong(), ctypes.c_longlong()
+        _check(load_library().bem_server_loop_stats(self._s, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
     @staticmethod
     def footprint(nx, ny):

@@ -4,6 +4,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+struct bem_ctx;
+
 namespace bem {
 
 // One FFT length of the plan: 2^logL points, first DIF stage radix 2^r0
@@ -55,8 +57,8 @@ struct Scalars {
   // fixed contact set S (band0 > band1: S is empty); written by k_box at the
   // start of a fixed-set solve.
   int band0, band1, col0, col1;
-  // Device-driven loop: iterations finished inside the captured while-loop
-  // graph, and the cap after which it stops (status SC_NOCONV).
+  // CG iterations counted on the device, and the cap after which the solve
+  // stops unconverged (the bound of the batched while-loop graph).
   int loops, max_loops;
   unsigned int cnt_a, cnt_c, cnt_e, cnt_r;  // last-block arrival counters
   // Sticky device error bits (kept across solves: init_scalars does not copy
@@ -120,24 +122,42 @@ struct PassArgs {
   double uscale;        // pass C: A / (Px Py)
   double* partA;        // per-CTA partials, 4 per CTA
   double* partC;
+  double* partE;        // per-CTA partials of the CG update (several-instance launches)
   Scalars* sc;
   unsigned int* kerr;   // sticky error word (may be null: errors then go unreported)
   int use_band;         // fixed-set CG loop: restrict the passes to rows sc->band0 .. band1
-  // Captured inside the body of a while-loop graph: the thread that finishes an
-  // iteration's scalars sets the loop condition `cond` (continue while not done).
-  int use_cond;
-  unsigned long long cond;  // cudaGraphConditionalHandle
 };
 
 template <typename T> void launch_pass_a(const PassArgs<T>& a, int mode, cudaStream_t s);
 template <typename T> void launch_pass_b(const PassArgs<T>& a, int mode, cudaStream_t s);
 template <typename T> void launch_pass_c(const PassArgs<T>& a, int mode, cudaStream_t s);
 
+// The same passes over n instances of one size class at once (blockIdx.y =
+// instance); a0 is any of them (its plan, row and column counts), arr the
+// device array of all n instances' arguments.  Only the CG-loop modes and the
+// persistent row passes (rows of a multiple of 16 elements) are provided.
+template <typename T> void launch_pass_a_mi(const PassArgs<T>& a0, int mode, const PassArgs<T>* arr, int n,
+                                            cudaStream_t s);
+template <typename T> void launch_pass_b_mi(const PassArgs<T>& a0, const PassArgs<T>* arr, int n, cudaStream_t s);
+template <typename T> void launch_pass_c_mi(const PassArgs<T>& a0, int mode, const PassArgs<T>* arr, int n,
+                                            cudaStream_t s);
+template <typename T> void launch_cg_update_mi(const PassArgs<T>* arr, int n, int ngrid, cudaStream_t s);
+// Sets the while-loop condition `cond` to "some instance is not done".
+template <typename T> void launch_batch_ctl(const PassArgs<T>* arr, int n, unsigned long long cond, cudaStream_t s);
+
+// Column pass on the tensor cores (tc_colpass.cu): an opt-in experiment
+// (BEM_TC_COLUMN_PASS=1) for the FP32 column pass of a 4096-point column over
+// the whole grid; tc_column_pass_applies tells whether a launch qualifies.
+bool tc_column_pass_enabled();
+bool tc_column_pass_applies(const PassArgs<float>& a);
+int launch_pass_b_tc(const PassArgs<float>& a, cudaStream_t s);
+int tc_column_pass_setup();  // once per device, when enabled
+
 // Elementwise kernels.
 template <typename T> void launch_pk_init(const Plan& pl, const double* h64, double d, T* c, T* p,
                                           T* t, int warm, int ngrid, cudaStream_t s);
 template <typename T> void launch_cg_update(const Plan& pl, Fields<T> f, double* part, Scalars* sc,
-                                            int ngrid, int use_cond, unsigned long long cond, cudaStream_t s);
+                                            int ngrid, cudaStream_t s);
 void launch_box(const Plan& pl, const uint8_t* S, Scalars* sc, cudaStream_t s);
 void launch_box_overlap(const Plan& pl, const double* h, double d, Scalars* sc, cudaStream_t s);
 void launch_box_copy64(const double* src, int nx, int ny, int x0, int y0, double* dst, int bx, int by,
@@ -172,6 +192,21 @@ bool plan_fits(const Plan& pl, int esize);
 // Once per device (with it current): shared-memory opt-ins of the pass kernels
 // and the quadrature nodes.  Returns BEM_OK or a BEM_E* code with the message set.
 int device_setup(int dev);
+
+// Batching of CG loops across solves that run concurrently in one process (the
+// request server): a thread whose solve reaches its CG loop joins the batcher;
+// the loops of all solves waiting at that moment run as one while-loop graph
+// per size class, every pass launched once over all of them (blockIdx.y =
+// instance), each instance stopping at its own convergence.  Results are
+// bitwise those of the solve run alone.
+struct LoopBatcher;
+LoopBatcher* batcher_create();               // on the current device
+void batcher_destroy(LoopBatcher* b);
+void batcher_enter(LoopBatcher* b);          // a thread starts a solve that may join
+void batcher_leave(LoopBatcher* b);          // ... and ends it
+void attach_batcher(::bem_ctx* h, LoopBatcher* b);  // a handle's loops (and its sub-contexts') join b
+// Adds the batched loop graphs launched so far and the solves' loops they carried.
+void batcher_stats(LoopBatcher* b, long long* launches, long long* instances);
 
 // Record `msg` as the thread's last error and return `code`.
 int set_error(int code, const char* msg);

@@ -503,7 +503,7 @@ __device__ __forceinline__ void pro_gather_staged(const T* st, const uint8_t* ss
 #define BEM_ROWP_BOUNDS(LOGL) __launch_bounds__((LOGL) >= 13 ? 1024 : 512, (LOGL) >= 13 ? 1 : BEM_ROWP_MIN_BLOCKS)
 
 template <typename T, int MODE, int LOGL>
-__global__ void BEM_ROWP_BOUNDS(LOGL) k_pass_ap(PassArgs<T> a) {
+__device__ __forceinline__ void pass_ap_body(const PassArgs<T>& a) {
   using Cx = C<T>;
   using F = FftC<T, LOGL>;
   constexpr int L = F::L, L8 = F::L8, M = L;
@@ -623,14 +623,26 @@ __global__ void BEM_ROWP_BOUNDS(LOGL) k_pass_ap(PassArgs<T> a) {
   }
 }
 
+// One launch of the persistent pass A; and the same over several instances of
+// one size class at once (blockIdx.y = instance, each with its own arguments,
+// fields, scalars and convergence flag).
+template <typename T, int MODE, int LOGL>
+__global__ void BEM_ROWP_BOUNDS(LOGL) k_pass_ap(PassArgs<T> a) {
+  pass_ap_body<T, MODE, LOGL>(a);
+}
+template <typename T, int MODE, int LOGL>
+__global__ void BEM_ROWP_BOUNDS(LOGL) k_pass_ap_mi(const PassArgs<T>* __restrict__ arr) {
+  pass_ap_body<T, MODE, LOGL>(arr[blockIdx.y]);
+}
+
 // ---------------------------------------------------------------------------
 // Pass B: nbB columns per CTA, Py/8 threads per column; columns kx = 0..M.
 #ifndef BEM_COL_MIN_BLOCKS
 #define BEM_COL_MIN_BLOCKS 2
 #endif
+#define BEM_COL_BOUNDS(LOGL) __launch_bounds__((LOGL) >= 13 ? 1024 : 512, (LOGL) >= 13 ? 1 : BEM_COL_MIN_BLOCKS)
 template <typename T, int MODE, int LOGL>
-__global__ void __launch_bounds__((LOGL) >= 13 ? 1024 : 512, (LOGL) >= 13 ? 1 : BEM_COL_MIN_BLOCKS)
-    k_pass_b(PassArgs<T> a) {
+__device__ __forceinline__ void pass_b_body(const PassArgs<T>& a) {
   using Cx = C<T>;
   using F = FftC<T, LOGL>;
   constexpr int L = F::L, L8 = F::L8, R0 = F::R0, hyq = (L >> 1) + 1;
@@ -725,6 +737,15 @@ __global__ void __launch_bounds__((LOGL) >= 13 ? 1024 : 512, (LOGL) >= 13 ? 1 : 
     }
   }
   (void)R0;
+}
+
+template <typename T, int MODE, int LOGL>
+__global__ void BEM_COL_BOUNDS(LOGL) k_pass_b(PassArgs<T> a) {
+  pass_b_body<T, MODE, LOGL>(a);
+}
+template <typename T, int MODE, int LOGL>
+__global__ void BEM_COL_BOUNDS(LOGL) k_pass_b_mi(const PassArgs<T>* __restrict__ arr) {
+  pass_b_body<T, MODE, LOGL>(arr[blockIdx.y]);
 }
 
 // Epilogue fields of pass C that are prefetched into shared memory at kernel
@@ -860,14 +881,8 @@ __device__ __forceinline__ void epi_apply(const PassArgs<T>& a, size_t i, T u, c
   }
 }
 
-// Device-driven CG loop (a while-loop node of a CUDA graph): the thread that
-// finishes an iteration's scalars sets the loop condition -- run the body again
-// while the solve is not done.  Every place that can set `done` calls it.
-__device__ __forceinline__ void set_loop_cond(int use, unsigned long long cond, const Scalars* sc) {
-  if (use) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, sc->done ? 0u : 1u);
-}
-// Count an iteration of the device-driven loop; past the cap the solve ends
-// unconverged (a bound on the loop whatever the iteration's outcome).
+// Count a CG iteration; past the cap the solve ends unconverged (a device-side
+// bound on the batched while-loop graph whatever the iteration's outcome).
 __device__ __forceinline__ void count_loop(Scalars* sc) {
   sc->loops += 1;
   if (!sc->done && sc->loops >= sc->max_loops) { sc->status = SC_NOCONV; sc->done = 1; }
@@ -877,8 +892,7 @@ __device__ __forceinline__ void count_loop(Scalars* sc) {
 // stopping test and beta after the gap pass, tau after the r pass, tau or the
 // initial residual of the fixed-set CG.
 template <int MODE>
-__device__ __forceinline__ void pass_c_finalize(Scalars* sc, const double (&s2)[2], const double (&s3)[3],
-                                                int use_cond, unsigned long long cond) {
+__device__ __forceinline__ void pass_c_finalize(Scalars* sc, const double (&s2)[2], const double (&s3)[3]) {
   if (MODE == C_PK_G) {
     sc->cnt_c = 0;
     const double G = s2[0], nic = s2[1];
@@ -907,7 +921,6 @@ __device__ __forceinline__ void pass_c_finalize(Scalars* sc, const double (&s2)[
       else { sc->beta = sc->delta * G / sc->G_old; sc->G_old = G; }
     }
     if (done) sc->done = 1;
-    set_loop_cond(use_cond, cond, sc);
   } else if (MODE == C_PK_R) {
     sc->cnt_a = 0;
     const double sgt = s2[0], srt = s2[1];
@@ -921,7 +934,6 @@ __device__ __forceinline__ void pass_c_finalize(Scalars* sc, const double (&s2)[
       sc->delta = 0.0;
     } else { sc->tau = sgt / srt; sc->have_tau = 1; }
     count_loop(sc);
-    set_loop_cond(use_cond, cond, sc);
   } else if (MODE == C_CG_R) {
     sc->cnt_a = 0;
     const double str = s2[0];
@@ -929,7 +941,6 @@ __device__ __forceinline__ void pass_c_finalize(Scalars* sc, const double (&s2)[
     if (!isfinite(str)) { sc->status = SC_NUMERIC; sc->done = 1; }
     else if (str <= 0.0) { sc->done = 1; }
     else sc->tau = sc->G / str;
-    set_loop_cond(use_cond, cond, sc);
   } else if (MODE == C_CG_G) {
     sc->cnt_a = 0;
     const double G = s2[0];
@@ -1099,7 +1110,7 @@ __global__ void BEM_ROW_BOUNDS(LOGL) k_pass_c(PassArgs<T> a) {
   double s3[3] = {0, 0, 0};
   if (MODE == C_PK_G) sum_partials<3>(a.partA, __ldcg(&sc->nA), s3, red);
   if (tid != 0) return;
-  pass_c_finalize<MODE>(sc, s2, s3, a.use_cond, a.cond);
+  pass_c_finalize<MODE>(sc, s2, s3);
 }
 
 // ---------------------------------------------------------------------------
@@ -1108,7 +1119,7 @@ __global__ void BEM_ROW_BOUNDS(LOGL) k_pass_c(PassArgs<T> a) {
 // as bulk copies (one per field row, on an mbarrier) while the current group
 // is transformed.  Used when rows are multiples of 16 elements.
 template <typename T, int MODE, int LOGL>
-__global__ void BEM_ROWP_BOUNDS(LOGL) k_pass_cp(PassArgs<T> a) {
+__device__ __forceinline__ void pass_cp_body(const PassArgs<T>& a) {
   using Cx = C<T>;
   using F = FftC<T, LOGL>;
   constexpr int L = F::L, L8 = F::L8, M = L;
@@ -1286,7 +1297,16 @@ __global__ void BEM_ROWP_BOUNDS(LOGL) k_pass_cp(PassArgs<T> a) {
   double s3[3] = {0, 0, 0};
   if (MODE == C_PK_G) sum_partials<3>(a.partA, __ldcg(&sc->nA), s3, red);
   if (tid != 0) return;
-  pass_c_finalize<MODE>(sc, s2, s3, a.use_cond, a.cond);
+  pass_c_finalize<MODE>(sc, s2, s3);
+}
+
+template <typename T, int MODE, int LOGL>
+__global__ void BEM_ROWP_BOUNDS(LOGL) k_pass_cp(PassArgs<T> a) {
+  pass_cp_body<T, MODE, LOGL>(a);
+}
+template <typename T, int MODE, int LOGL>
+__global__ void BEM_ROWP_BOUNDS(LOGL) k_pass_cp_mi(const PassArgs<T>* __restrict__ arr) {
+  pass_cp_body<T, MODE, LOGL>(arr[blockIdx.y]);
 }
 
 // ---------------------------------------------------------------------------
@@ -1340,8 +1360,7 @@ __device__ __forceinline__ T cg_update_one(T* __restrict__ p, T* __restrict__ g,
 // the new G, beta and the convergence test.  Four elements per thread and
 // trip through vector loads when the pointers allow it.
 template <typename T>
-__global__ void k_cg_update(int nx, Fields<T> f, double* part, Scalars* sc, int use_cond,
-                            unsigned long long cond) {
+__device__ __forceinline__ void cg_update_body(int nx, const Fields<T>& f, double* part, Scalars* sc) {
   __shared__ double red[3 * 32];
   __shared__ int lastflag;
   if (sc->done) return;
@@ -1395,7 +1414,26 @@ __global__ void k_cg_update(int nx, Fields<T> f, double* part, Scalars* sc, int 
     sc->G = Gn;
   }
   count_loop(sc);
-  set_loop_cond(use_cond, cond, sc);
+}
+
+template <typename T>
+__global__ void k_cg_update(int nx, Fields<T> f, double* part, Scalars* sc) {
+  cg_update_body<T>(nx, f, part, sc);
+}
+template <typename T>
+__global__ void k_cg_update_mi(const PassArgs<T>* __restrict__ arr) {
+  const PassArgs<T>& a = arr[blockIdx.y];
+  cg_update_body<T>(a.pl.nx, a.f, a.partE, a.sc);
+}
+
+// Loop condition of a while-loop graph over several instances: run the body
+// again while any instance's solve is not done.
+template <typename T>
+__global__ void k_batch_ctl(const PassArgs<T>* __restrict__ arr, int n, unsigned long long cond) {
+  int live = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) live |= !(*(volatile int*)&arr[i].sc->done);
+  live = __syncthreads_or(live);
+  if (threadIdx.x == 0) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, live ? 1u : 0u);
 }
 
 // Detach every element of S with tensile stress -p > p_crit (Eq. 24).
@@ -1608,6 +1646,79 @@ void launch_c_mode(const PassArgs<T>& a, cudaStream_t s) {
   }
 }
 
+// Several-instance launches (blockIdx.y = instance).  Every instance has the
+// plan `a0` has (one size class); each keeps the grid.x its single launch
+// would have, so its partial sums, and so its results, are the same bitwise.
+template <typename T, int MODE>
+void launch_a_mode_mi(const PassArgs<T>& a0, const PassArgs<T>* arr, int n, cudaStream_t s) {
+  const dim3 block(a0.pl.threadsA);
+  const int groups = (a0.nrows_in + a0.pl.nbA - 1) / a0.pl.nbA;
+  const size_t smem = ((a0.pl.smemA + 15) & ~(size_t)15) + pro_stage_bytes<T, MODE>(a0.pl.nbA, a0.ncols_in);
+  switch (a0.pl.gA.logL) {
+#define BEM_CASE(LG)                                                                        \
+  case LG: {                                                                                \
+    const int occ = resident_ctas(k_pass_ap<T, MODE, LG>, a0.pl.threadsA, smem);           \
+    const dim3 grid(std::min(groups, a0.pl.nsm * occ), n);                                  \
+    k_pass_ap_mi<T, MODE, LG><<<grid, block, smem, s>>>(arr);                               \
+  } break;
+    BEM_LOGL_CASES_A(BEM_CASE)
+#undef BEM_CASE
+  }
+}
+template <typename T, int MODE>
+void launch_c_mode_mi(const PassArgs<T>& a0, const PassArgs<T>* arr, int n, cudaStream_t s) {
+  const dim3 block(a0.pl.threadsA);
+  const int groups = a0.pl.gridA;
+  const size_t smem = ((a0.pl.smemC + 15) & ~(size_t)15) +
+                      ((sizeof(C<T>) * (size_t)(a0.pl.M + 1) * a0.pl.nbA + 15) & ~(size_t)15) +
+                      epi_stage_bytes<T, MODE>(a0.pl.nbA, a0.pl.nx);
+  switch (a0.pl.gA.logL) {
+#define BEM_CASE(LG)                                                                        \
+  case LG: {                                                                                \
+    const int occ = resident_ctas(k_pass_cp<T, MODE, LG>, a0.pl.threadsA, smem);           \
+    const dim3 grid(std::min(groups, a0.pl.nsm * occ), n);                                  \
+    k_pass_cp_mi<T, MODE, LG><<<grid, block, smem, s>>>(arr);                               \
+  } break;
+    BEM_LOGL_CASES_A(BEM_CASE)
+#undef BEM_CASE
+  }
+}
+template <typename T>
+void launch_pass_a_mi(const PassArgs<T>& a0, int mode, const PassArgs<T>* arr, int n, cudaStream_t s) {
+  if (mode == A_PK_P) launch_a_mode_mi<T, A_PK_P>(a0, arr, n, s);
+  else if (mode == A_PK_T) launch_a_mode_mi<T, A_PK_T>(a0, arr, n, s);
+  else if (mode == A_CG_T) launch_a_mode_mi<T, A_CG_T>(a0, arr, n, s);
+}
+template <typename T>
+void launch_pass_b_mi(const PassArgs<T>& a0, const PassArgs<T>* arr, int n, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (n == 1 && tc_column_pass_enabled() && tc_column_pass_applies(a0)) {
+      launch_pass_b_tc(a0, s);
+      return;
+    }
+  }
+  const dim3 grid(a0.pl.gridB, n), block(a0.pl.threadsB);
+  switch (a0.pl.gB.logL) {
+#define BEM_CASE(LG) case LG: k_pass_b_mi<T, B_CONV, LG><<<grid, block, a0.pl.smemB, s>>>(arr); break;
+    BEM_LOGL_CASES_B(BEM_CASE)
+#undef BEM_CASE
+  }
+}
+template <typename T>
+void launch_pass_c_mi(const PassArgs<T>& a0, int mode, const PassArgs<T>* arr, int n, cudaStream_t s) {
+  if (mode == C_PK_G) launch_c_mode_mi<T, C_PK_G>(a0, arr, n, s);
+  else if (mode == C_PK_R) launch_c_mode_mi<T, C_PK_R>(a0, arr, n, s);
+  else if (mode == C_CG_R) launch_c_mode_mi<T, C_CG_R>(a0, arr, n, s);
+}
+template <typename T>
+void launch_cg_update_mi(const PassArgs<T>* arr, int n, int ngrid, cudaStream_t s) {
+  k_cg_update_mi<T><<<dim3(ngrid, n), 256, 0, s>>>(arr);
+}
+template <typename T>
+void launch_batch_ctl(const PassArgs<T>* arr, int n, unsigned long long cond, cudaStream_t s) {
+  k_batch_ctl<T><<<1, 256, 0, s>>>(arr, n, cond);
+}
+
 template <typename T>
 void launch_pass_a(const PassArgs<T>& a, int mode, cudaStream_t s) {
   switch (mode) {
@@ -1622,8 +1733,17 @@ void launch_pass_a(const PassArgs<T>& a, int mode, cudaStream_t s) {
 }
 template <typename T>
 void launch_pass_b(const PassArgs<T>& a, int mode, cudaStream_t s) {
-  if (mode == B_SPECTRUM) launch_b_mode<T, B_SPECTRUM>(a, s);
-  else launch_b_mode<T, B_CONV>(a, s);
+  if (mode == B_SPECTRUM) {
+    launch_b_mode<T, B_SPECTRUM>(a, s);
+    return;
+  }
+  if constexpr (sizeof(T) == 4) {
+    if (tc_column_pass_enabled() && tc_column_pass_applies(a)) {
+      launch_pass_b_tc(a, s);
+      return;
+    }
+  }
+  launch_b_mode<T, B_CONV>(a, s);
 }
 template <typename T>
 void launch_pass_c(const PassArgs<T>& a, int mode, cudaStream_t s) {
@@ -1662,6 +1782,9 @@ cudaError_t set_smem_attrs_a(int bytes) {
   BEM_ATTR((k_pass_ap<T, A_PK_P, LG>))        \
   BEM_ATTR((k_pass_ap<T, A_PK_T, LG>))        \
   BEM_ATTR((k_pass_ap<T, A_CG_T, LG>))        \
+  BEM_ATTR((k_pass_ap_mi<T, A_PK_P, LG>))     \
+  BEM_ATTR((k_pass_ap_mi<T, A_PK_T, LG>))     \
+  BEM_ATTR((k_pass_ap_mi<T, A_CG_T, LG>))     \
   if constexpr (sizeof(T) == 8) { BEM_ATTR((k_pass_a<T, A_TORUS, LG>)) }
   BEM_LOGL_CASES_A(BEM_CASE)
 #undef BEM_CASE
@@ -1670,7 +1793,8 @@ cudaError_t set_smem_attrs_a(int bytes) {
 template <typename T>
 cudaError_t set_smem_attrs_b(int bytes) {
   cudaError_t e = cudaSuccess, r;
-#define BEM_CASE(LG) BEM_ATTR((k_pass_b<T, B_CONV, LG>)) BEM_ATTR((k_pass_b<T, B_SPECTRUM, LG>))
+#define BEM_CASE(LG) \
+  BEM_ATTR((k_pass_b<T, B_CONV, LG>)) BEM_ATTR((k_pass_b<T, B_SPECTRUM, LG>)) BEM_ATTR((k_pass_b_mi<T, B_CONV, LG>))
   BEM_LOGL_CASES_B(BEM_CASE)
 #undef BEM_CASE
   return e;
@@ -1690,7 +1814,10 @@ cudaError_t set_smem_attrs_c(int bytes) {
   BEM_ATTR((k_pass_cp<T, C_PK_R, LG>))        \
   BEM_ATTR((k_pass_cp<T, C_CG_R, LG>))        \
   BEM_ATTR((k_pass_cp<T, C_CG_G, LG>))        \
-  BEM_ATTR((k_pass_cp<T, C_GAP, LG>))
+  BEM_ATTR((k_pass_cp<T, C_GAP, LG>))         \
+  BEM_ATTR((k_pass_cp_mi<T, C_PK_G, LG>))     \
+  BEM_ATTR((k_pass_cp_mi<T, C_PK_R, LG>))     \
+  BEM_ATTR((k_pass_cp_mi<T, C_CG_R, LG>))
   BEM_LOGL_CASES_A(BEM_CASE)
 #undef BEM_CASE
   return e;
@@ -1724,9 +1851,8 @@ void launch_box_scatter(const T* bp, T* p, int nx, int ny, int x0, int y0, int b
   k_box_scatter<T><<<ew_grid((size_t)nb), 256, 0, s>>>(bp, p, nx, ny, x0, y0, lbx, nb);
 }
 template <typename T>
-void launch_cg_update(const Plan& pl, Fields<T> f, double* part, Scalars* sc, int ngrid, int use_cond,
-                      unsigned long long cond, cudaStream_t s) {
-  k_cg_update<T><<<ngrid, 256, 0, s>>>(pl.nx, f, part, sc, use_cond, cond);
+void launch_cg_update(const Plan& pl, Fields<T> f, double* part, Scalars* sc, int ngrid, cudaStream_t s) {
+  k_cg_update<T><<<ngrid, 256, 0, s>>>(pl.nx, f, part, sc);
 }
 template <typename T>
 void launch_detach(const Plan& pl, Fields<T> f, double* part, Scalars* sc, int ngrid,
@@ -1763,12 +1889,15 @@ void launch_mask_field(T* x, const uint8_t* S, size_t n, cudaStream_t s) {
 
 #define BEM_INSTANTIATE_A(T)                                                                   \
   template void launch_pass_a<T>(const PassArgs<T>&, int, cudaStream_t);                      \
+  template void launch_pass_a_mi<T>(const PassArgs<T>&, int, const PassArgs<T>*, int, cudaStream_t); \
   template cudaError_t set_smem_attrs_a<T>(int);
 #define BEM_INSTANTIATE_B(T)                                                                   \
   template void launch_pass_b<T>(const PassArgs<T>&, int, cudaStream_t);                      \
+  template void launch_pass_b_mi<T>(const PassArgs<T>&, const PassArgs<T>*, int, cudaStream_t); \
   template cudaError_t set_smem_attrs_b<T>(int);
 #define BEM_INSTANTIATE_C(T)                                                                   \
   template void launch_pass_c<T>(const PassArgs<T>&, int, cudaStream_t);                      \
+  template void launch_pass_c_mi<T>(const PassArgs<T>&, int, const PassArgs<T>*, int, cudaStream_t); \
   template cudaError_t set_smem_attrs_c<T>(int);
 #define BEM_INSTANTIATE_EW(T)                                                                  \
   template void launch_pk_init<T>(const Plan&, const double*, double, T*, T*, T*, int, int,    \
@@ -1776,8 +1905,8 @@ void launch_mask_field(T* x, const uint8_t* S, size_t n, cudaStream_t s) {
   template void launch_box_gather<T>(const T*, const T*, const uint8_t*, int, int, int, int, T*, T*, \
                                      uint8_t*, int, int, cudaStream_t);                         \
   template void launch_box_scatter<T>(const T*, T*, int, int, int, int, int, int, cudaStream_t); \
-  template void launch_cg_update<T>(const Plan&, Fields<T>, double*, Scalars*, int, int,       \
-                                    unsigned long long, cudaStream_t);                         \
+  template void launch_cg_update<T>(const Plan&, Fields<T>, double*, Scalars*, int,            \
+                                    cudaStream_t);                                             \
   template void launch_detach<T>(const Plan&, Fields<T>, double*, Scalars*, int, cudaStream_t); \
   template void launch_stats<T>(const Plan&, const T*, const T*, const uint8_t*, int, double*, \
                                 double*, int, cudaStream_t);                                   \
@@ -1785,6 +1914,8 @@ void launch_mask_field(T* x, const uint8_t* S, size_t n, cudaStream_t s) {
   template void launch_convert_out<T>(const T*, double*, size_t, cudaStream_t);               \
   template void launch_offset<T>(const double*, double, T*, size_t, cudaStream_t);            \
   template void launch_set_from_p<T>(const T*, uint8_t*, size_t, cudaStream_t);               \
-  template void launch_mask_field<T>(T*, const uint8_t*, size_t, cudaStream_t);
+  template void launch_mask_field<T>(T*, const uint8_t*, size_t, cudaStream_t);                \
+  template void launch_cg_update_mi<T>(const PassArgs<T>*, int, int, cudaStream_t);            \
+  template void launch_batch_ctl<T>(const PassArgs<T>*, int, unsigned long long, cudaStream_t);
 
 }  // namespace bem

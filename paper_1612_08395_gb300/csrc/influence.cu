@@ -11,7 +11,9 @@
 // integrand cosh^-k is smooth, so composite Gauss-Legendre converges fast.
 // F is odd in each argument.  Away from the singularity the integrand is
 // analytic on the element and tensor Gauss-Legendre rules are used directly,
-// with fewer points the farther the element.
+// with fewer points the farther the element; the distance is counted in units
+// of the element's longer side, so elongated elements near the singularity
+// take the corner formula.
 #include <math.h>
 #include <cuda_runtime.h>
 
@@ -126,7 +128,12 @@ __global__ void k_influence(double* Kq, int hx, int hy, double dx, double dy, do
   if (di >= hx || dj >= hy) return;
   const double a0 = (di - 0.5) * dx, a1 = (di + 0.5) * dx;
   const double b0 = (dj - 0.5) * dy, b1 = (dj + 0.5) * dy;
-  const int far = di > dj ? di : dj;
+  // distance class of the element: its index distance, but for elongated
+  // elements never more than its physical distance from the singularity in
+  // units of its longer side (a long element can reach close to the origin)
+  const double ea = fmax(0.0, a0), eb = fmax(0.0, b0), side = fmax(dx, dy);
+  const double phys = sqrt(ea * ea + eb * eb) / side + 0.5;
+  const double far = fmin((double)(di > dj ? di : dj), phys);
   double v;
   if (far <= NEAR) {
     v = f_corner(a1, b1, k) - f_corner(a0, b1, k) - f_corner(a1, b0, k) + f_corner(a0, b0, k);

@@ -16,6 +16,7 @@
 // which bem_set_material updates.  Each solve is deterministic and touches
 // only its own handle, so its result is the same alone and in any mix.
 #include <math.h>
+#include <stdlib.h>
 
 #include <algorithm>
 #include <chrono>
@@ -90,6 +91,10 @@ struct DevPool {
   size_t used = 0;          // bytes of cached handles (busy or idle) + reservations
   std::list<Cached> cache;  // front = most recently used
   int workers = 0, busy = 0;
+  // CG loops of the jobs running here join this batcher (null: each job
+  // launches its own loops; BEM_BATCH_LOOPS=0 switches batching off)
+  bem::LoopBatcher* batcher = nullptr;
+  bool batcher_tried = false;
 };
 
 }  // namespace
@@ -159,6 +164,16 @@ void device_views(const bem_server* s, const Key& k, std::vector<bem_device_view
 
 void worker_main(bem_server* s, int di) {
   cudaSetDevice(s->devs[di].device);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    DevPool& dev = s->devs[di];
+    if (!dev.batcher_tried) {
+      dev.batcher_tried = true;
+      const char* env = getenv("BEM_BATCH_LOOPS");
+      if (!(env && env[0] == '0')) dev.batcher = bem::batcher_create();
+    }
+  }
+  bem::LoopBatcher* batcher = s->devs[di].batcher;
   std::vector<bem_device_view> views;
   for (;;) {
     Pending p;
@@ -219,9 +234,15 @@ void worker_main(bem_server* s, int di) {
     } else {
       rc = bem_set_material(h, p.job.nu, p.job.E0, p.job.c0);
     }
-    if (rc == BEM_OK)
+    if (rc == BEM_OK) {
+      if (batcher) {
+        bem::attach_batcher(h, batcher);
+        bem::batcher_enter(batcher);
+      }
       rc = bem_sweep(h, p.job.profile, p.job.d_steps, p.job.nsteps, p.job.dgamma, &p.job.opts,
                      p.job.per_step, p.job.final_pressure);
+      if (batcher) bem::batcher_leave(batcher);
+    }
     c.t_end = now_s(s->t0);
     c.status = rc;
     {
@@ -390,6 +411,16 @@ extern "C" int bem_server_pending(bem_server_handle s) {
   return (int)s->queue.size() + s->running;
 }
 
+extern "C" int bem_server_loop_stats(bem_server_handle s, long long* launches, long long* loops) {
+  if (!s || !launches || !loops) return bem::set_error(BEM_EINVAL, "bem_server_loop_stats: NULL argument");
+  *launches = 0;
+  *loops = 0;
+  std::lock_guard<std::mutex> lk(s->mu);
+  for (DevPool& d : s->devs)
+    if (d.batcher) bem::batcher_stats(d.batcher, launches, loops);
+  return BEM_OK;
+}
+
 extern "C" size_t bem_server_bytes(bem_server_handle s) {
   if (!s) return 0;
   std::lock_guard<std::mutex> lk(s->mu);
@@ -411,6 +442,7 @@ extern "C" void bem_server_destroy(bem_server_handle s) {
   for (DevPool& d : s->devs) {
     cudaSetDevice(d.device);
     for (auto& c : d.cache) bem_destroy(c.h);
+    bem::batcher_destroy(d.batcher);
   }
   if (have_prev) cudaSetDevice(prev);
   delete s;

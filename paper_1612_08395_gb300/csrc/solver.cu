@@ -9,6 +9,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <chrono>
+#include <condition_variable>
 #include <map>
 #include <mutex>
 #include <vector>
@@ -75,8 +77,8 @@ namespace {
 #ifndef BEM_CHUNK
 #define BEM_CHUNK 8
 #endif
-constexpr int kChunk = BEM_CHUNK;  // CG iterations of the timed (event-recording) chunk graph
-// CG iterations per body of the device-driven while-loop graph
+constexpr int kChunk = BEM_CHUNK;  // CG iterations per captured graph launch
+// CG iterations per body of the while-loop graph of batched loops
 #ifndef BEM_LOOP_BODY
 #define BEM_LOOP_BODY 4
 #endif
@@ -91,9 +93,7 @@ constexpr int kLoopBody = BEM_LOOP_BODY;
 template <typename T> struct PrecFields {
   T *p = nullptr, *g = nullptr, *t = nullptr, *r = nullptr, *c = nullptr;
   bool ready = false;
-  // [0]: the device-driven loop (while node), [1]: a chunk of kChunk iterations
-  // with event records around the passes of its first iteration (pass timing)
-  cudaGraphExec_t pk_graph[2] = {nullptr, nullptr}, cg_graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t pk_graph[2] = {nullptr, nullptr}, cg_graph[2] = {nullptr, nullptr};  // [timed]
 };
 
 int ilog2(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
@@ -188,6 +188,8 @@ int device_setup(int dev) {
   if (ea == cudaSuccess) ea = set_smem_attrs_c<double>(smem_max);
   if (ea != cudaSuccess) return fail(BEM_ECUDA, "shared-memory opt-in failed: %s", cudaGetErrorString(ea));
   if (influence_init_nodes() != 0) return fail(BEM_ECUDA, "quadrature nodes upload failed");
+  const int rc = tc_column_pass_setup();
+  if (rc != BEM_OK) return rc;
   init_done[dev] = true;
   return BEM_OK;
 }
@@ -233,6 +235,9 @@ struct bem_ctx {
   // set fits a box of at most half their size); they share the parent's stream.
   bool is_sub = false, own_stream = true;
   std::vector<bem_ctx*> subs;
+  // CG loops join this batcher when set (concurrent solves of the server)
+  bem::LoopBatcher* batcher = nullptr;
+  cudaEvent_t ev_ready = nullptr;  // this context's work before its batched loop
 };
 
 static int create_ctx(int Nx, int Ny, double dx, double dy, double k, double nu, double E0, double c0,
@@ -303,6 +308,7 @@ PassArgs<T> make_args(bem_ctx* h) {
   a.uscale = h->A / ((double)h->px * (double)h->py);
   a.partA = h->part;
   a.partC = h->partC;
+  a.partE = h->partE;
   a.sc = h->sc;
   a.kerr = &h->sc->kerr;
   return a;
@@ -401,12 +407,14 @@ void conv_plain(bem_ctx* h, const T* x, T* dst, cudaStream_t s) {
 
 // The passes of `iters` CG iterations, captured on the handle's stream; with
 // `ev`, event records around the three passes of the first iteration.
+// Rows of a multiple of 16 elements (the persistent row passes): the CG loop
+// may join a batch of several instances.
+bool loop_batchable(const bem_ctx* h) { return (h->nx & 15) == 0; }
+
 template <typename T>
-int capture_iterations(bem_ctx* h, bool pk, int iters, cudaEvent_t* ev, int use_cond, unsigned long long cond) {
+int capture_iterations(bem_ctx* h, bool pk, int iters, cudaEvent_t* ev) {
   PassArgs<T> a = make_args<T>(h);
   a.use_band = pk ? 0 : 1;  // fixed-set CG: only the contact band's rows
-  a.use_cond = use_cond;
-  a.cond = cond;
   Fields<T> f = a.f;
   for (int it = 0; it < iters; ++it) {
     const bool mark = ev && it == 0;
@@ -430,24 +438,24 @@ int capture_iterations(bem_ctx* h, bool pk, int iters, cudaEvent_t* ev, int use_
       launch_pass_c<T>(a, C_PK_R, h->stream);
       CAPTURE_CHECK("pass C (t)");
     } else {
-      launch_cg_update<T>(a.pl, f, h->partE, h->sc, h->ew_ngrid, use_cond, cond, h->stream);
+      launch_cg_update<T>(a.pl, f, h->partE, h->sc, h->ew_ngrid, h->stream);
       CAPTURE_CHECK("cg update");
     }
   }
   return BEM_OK;
 }
 
-// Timed chunk: kChunk iterations with event records (BEM_FLAG_TIME_PASSES).
+// A chunk of kChunk CG iterations as one graph; with `timed`, event records
+// around the three passes of its first iteration (BEM_FLAG_TIME_PASSES).
 template <typename T>
-int capture_timed(bem_ctx* h, bool pk, cudaGraphExec_t* out) {
-  cudaGraph_t graph;
+int capture_chunk(bem_ctx* h, bool pk, bool timed, cudaGraphExec_t* out) {
+  cudaGraph_t graph = nullptr;
   cudaEvent_t* ev = h->ev[pk ? 0 : 1];
-  if (!ev[0])
+  if (timed && !ev[0])
     for (int i = 0; i < 4; ++i) CK(cudaEventCreate(&ev[i]));
   CK(cudaGetLastError());
   CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-  const int rc = capture_iterations<T>(h, pk, kChunk, ev, 0, 0);
-  graph = nullptr;
+  const int rc = capture_iterations<T>(h, pk, kChunk, timed ? ev : nullptr);
   cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
   if (rc != BEM_OK || e != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
@@ -459,48 +467,6 @@ int capture_timed(bem_ctx* h, bool pk, cudaGraphExec_t* out) {
   return BEM_OK;
 }
 
-// The device-driven CG loop: one graph whose while node repeats a body of
-// kLoopBody iterations until the kernel that finishes an iteration's scalars
-// clears the condition (the solve is done: converged, capped or failed).  One
-// launch runs the whole solve; the host reads the scalars once, at the end.
-template <typename T>
-int capture_loop(bem_ctx* h, bool pk, cudaGraphExec_t* out) {
-  cudaGraph_t graph = nullptr;
-  CK(cudaGetLastError());
-  CK(cudaGraphCreate(&graph, 0));
-  cudaGraphConditionalHandle cond;
-  cudaError_t e = cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault);
-  cudaGraphNodeParams np = {};
-  np.type = cudaGraphNodeTypeConditional;
-  np.conditional.handle = cond;
-  np.conditional.type = cudaGraphCondTypeWhile;
-  np.conditional.size = 1;
-  cudaGraphNode_t node;
-  if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
-  if (e != cudaSuccess) {
-    cudaGraphDestroy(graph);
-    return fail(BEM_ECUDA, "while-loop graph set-up failed: %s", cudaGetErrorString(e));
-  }
-  cudaGraph_t body = np.conditional.phGraph_out[0];
-  e = cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-  if (e != cudaSuccess) {
-    cudaGraphDestroy(graph);
-    return fail(BEM_ECUDA, "loop body capture failed: %s", cudaGetErrorString(e));
-  }
-  int rc = capture_iterations<T>(h, pk, kLoopBody, nullptr, 1, (unsigned long long)cond);
-  cudaGraph_t body_out = nullptr;
-  e = cudaStreamEndCapture(h->stream, &body_out);
-  if (rc != BEM_OK || e != cudaSuccess) {
-    cudaGraphDestroy(graph);
-    return rc != BEM_OK ? rc : fail(BEM_ECUDA, "loop body capture failed: %s", cudaGetErrorString(e));
-  }
-  e = cudaGraphInstantiate(out, graph, 0);
-  cudaGraphDestroy(graph);
-  if (e != cudaSuccess) return fail(BEM_ECUDA, "loop graph instantiate failed: %s", cudaGetErrorString(e));
-  return BEM_OK;
-}
-
-// Run chunks of the captured loop until the device sets `done`.
 // Algorithmic bytes and flops of one launch of each pass (A, B, C) on `rows`
 // grid rows, for element size es: field reads and writes of the mode, W
 // written / read / rewritten, the spectrum quarter; FFT flops 5 L log2 L per
@@ -518,37 +484,289 @@ void add_pass_work(bem_ctx* h, bool pk, int rows, int es) {
   h->pass_flops[2] += rows * (0.5 * fm + 20 * M);
 }
 
-// Run the solve's CG loop until the device sets `done`: under
-// BEM_FLAG_TIME_PASSES first one timed chunk (its passes' durations and work
-// are accumulated), then the device-driven loop graph.
-int run_loop(bem_ctx* h, cudaGraphExec_t g_loop, cudaGraphExec_t g_timed, bool pk, int es) {
-  const int kpi = pk ? 6 : 4;  // kernels per iteration
-  if (h->timing) {
-    CK(cudaGraphLaunch(g_timed, h->stream));
-    h->launches += (unsigned long long)kChunk * kpi;
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Batching of CG loops across concurrent solves.
+namespace bem {
+
+struct LoopReq {
+  bem_ctx* h = nullptr;
+  bool pk = false;
+  int es = 4;
+  PassArgs<float> a32{};
+  PassArgs<double> a64{};
+  bool done = false;
+  bool solo = false;  // no other loop of its size class was waiting: run it alone
+  int rc = BEM_OK;
+};
+
+struct LoopBatcher {
+  int device = 0;
+  std::mutex mu;
+  std::condition_variable cv;
+  int active = 0;     // threads inside a solve (they may join)
+  bool leading = false;
+  std::vector<LoopReq*> waiting;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev = nullptr;
+  struct Entry {
+    cudaGraphExec_t exec = nullptr;
+    void* d_args = nullptr;
+  };
+  std::map<std::vector<int>, Entry> graphs;  // size class + instance count
+  long long launches = 0, instances = 0;     // batched loop graphs launched, loops they carried
+};
+
+LoopBatcher* batcher_create() {
+  LoopBatcher* b = new LoopBatcher();
+  cudaGetDevice(&b->device);
+  if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return nullptr;
+  }
+  return b;
+}
+
+void batcher_destroy(LoopBatcher* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  for (auto& kv : b->graphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.d_args) cudaFree(kv.second.d_args);
+  }
+  cudaEventDestroy(b->ev);
+  cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+void batcher_enter(LoopBatcher* b) {
+  std::lock_guard<std::mutex> lk(b->mu);
+  b->active++;
+}
+
+void batcher_leave(LoopBatcher* b) {
+  std::lock_guard<std::mutex> lk(b->mu);
+  b->active--;
+  b->cv.notify_all();  // the waiting loops may now be all there are
+}
+
+void batcher_stats(LoopBatcher* b, long long* launches, long long* instances) {
+  std::lock_guard<std::mutex> lk(b->mu);
+  *launches += b->launches;
+  *instances += b->instances;
+}
+
+void attach_batcher(::bem_ctx* h, LoopBatcher* b) {
+  h->batcher = b;
+  for (::bem_ctx* c : h->subs) attach_batcher(c, b);
+}
+
+}  // namespace bem
+
+namespace {
+
+// Size class of a loop request: requests with equal keys share every launch
+// shape, so one several-instance launch per pass serves them all.
+std::vector<int> loop_key(const LoopReq& r) {
+  const Plan& pl = r.es == 4 ? r.a32.pl : r.a64.pl;
+  return {r.es, r.pk ? 1 : 0, pl.nx, pl.ny, pl.px, pl.py, pl.nbA, pl.nbB, r.h->ew_ngrid};
+}
+
+// The while-loop graph of n instances of one size class: kLoopBody iterations
+// of several-instance passes, then the condition kernel (any instance live).
+template <typename T>
+int capture_loop_mi(LoopBatcher* b, const PassArgs<T>& a0, bool pk, int n, int ew_ngrid, const PassArgs<T>* arr,
+                    cudaGraphExec_t* out) {
+  cudaGraph_t graph = nullptr;
+  CK(cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle cond;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = cond;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+  if (e == cudaSuccess)
+    e = cudaStreamBeginCaptureToGraph(b->stream, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return fail(BEM_ECUDA, "batched loop graph set-up failed: %s", cudaGetErrorString(e));
+  }
+  for (int it = 0; it < kLoopBody; ++it) {
+    if (pk) {
+      launch_pass_a_mi<T>(a0, A_PK_P, arr, n, b->stream);
+      launch_pass_b_mi<T>(a0, arr, n, b->stream);
+      launch_pass_c_mi<T>(a0, C_PK_G, arr, n, b->stream);
+      launch_pass_a_mi<T>(a0, A_PK_T, arr, n, b->stream);
+      launch_pass_b_mi<T>(a0, arr, n, b->stream);
+      launch_pass_c_mi<T>(a0, C_PK_R, arr, n, b->stream);
+    } else {
+      launch_pass_a_mi<T>(a0, A_CG_T, arr, n, b->stream);
+      launch_pass_b_mi<T>(a0, arr, n, b->stream);
+      launch_pass_c_mi<T>(a0, C_CG_R, arr, n, b->stream);
+      launch_cg_update_mi<T>(arr, n, ew_ngrid, b->stream);
+    }
+  }
+  launch_batch_ctl<T>(arr, n, (unsigned long long)cond, b->stream);
+  const cudaError_t le = cudaPeekAtLastError();
+  cudaGraph_t body_out = nullptr;
+  e = cudaStreamEndCapture(b->stream, &body_out);
+  if (le != cudaSuccess || e != cudaSuccess) {
+    cudaGetLastError();
+    cudaGraphDestroy(graph);
+    return fail(BEM_ECUDA, "batched loop capture failed: %s", cudaGetErrorString(le != cudaSuccess ? le : e));
+  }
+  e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(BEM_ECUDA, "batched loop instantiate failed: %s", cudaGetErrorString(e));
+  return BEM_OK;
+}
+
+// Launch one size class's requests as one graph on the batcher's stream, after
+// each instance's earlier work; each instance's stream then waits for it.
+template <typename T>
+int launch_group(LoopBatcher* b, std::vector<LoopReq*>& g, const std::vector<int>& key) {
+  const int n = (int)g.size();
+  std::vector<PassArgs<T>> host(n);
+  for (int i = 0; i < n; ++i) {
+    host[i] = sizeof(T) == 4 ? *reinterpret_cast<const PassArgs<T>*>(&g[i]->a32)
+                             : *reinterpret_cast<const PassArgs<T>*>(&g[i]->a64);
+    CK(cudaStreamWaitEvent(b->stream, g[i]->h->ev_ready, 0));
+  }
+  std::vector<int> gk = key;
+  gk.push_back(n);
+  LoopBatcher::Entry& en = b->graphs[gk];
+  if (!en.d_args) CK(cudaMalloc(&en.d_args, sizeof(PassArgs<T>) * (size_t)n));
+  if (!en.exec) {
+    CKR(capture_loop_mi<T>(b, host[0], g[0]->pk, n, g[0]->h->ew_ngrid,
+                           reinterpret_cast<const PassArgs<T>*>(en.d_args), &en.exec));
+  }
+  // pageable source: the copy is staged before the call returns
+  CK(cudaMemcpyAsync(en.d_args, host.data(), sizeof(PassArgs<T>) * (size_t)n, cudaMemcpyHostToDevice, b->stream));
+  CK(cudaGraphLaunch(en.exec, b->stream));
+  b->launches += 1;
+  b->instances += n;
+  CK(cudaEventRecord(b->ev, b->stream));
+  for (LoopReq* r : g) CK(cudaStreamWaitEvent(r->h->stream, b->ev, 0));
+  return BEM_OK;
+}
+
+int launch_batch(LoopBatcher* b, std::vector<LoopReq*>& reqs) {
+  std::map<std::vector<int>, std::vector<LoopReq*>> groups;
+  for (LoopReq* r : reqs) groups[loop_key(*r)].push_back(r);
+  for (auto& kv : groups) {
+    if (kv.second.size() == 1) {  // nothing to share a launch with: the solve runs its own loop
+      kv.second[0]->solo = true;
+      continue;
+    }
+    const int rc = kv.first[0] == 4 ? launch_group<float>(b, kv.second, kv.first)
+                                    : launch_group<double>(b, kv.second, kv.first);
+    if (rc != BEM_OK) return rc;
+  }
+  return BEM_OK;
+}
+
+// The solve's CG loop as part of a batch: join, and either wait for a leader or
+// lead: take every waiting request once all solves in flight wait (or after a
+// short wait for the rest) and launch them.
+int run_loop_batched(bem_ctx* h, bool pk, int es, bool* solo) {
+  LoopBatcher* b = h->batcher;
+  LoopReq r;
+  r.h = h;
+  r.pk = pk;
+  r.es = es;
+  if (es == 4) {
+    r.a32 = make_args<float>(h);
+    r.a32.use_band = pk ? 0 : 1;
+  } else {
+    r.a64 = make_args<double>(h);
+    r.a64.use_band = pk ? 0 : 1;
+  }
+  if (!h->ev_ready) CK(cudaEventCreateWithFlags(&h->ev_ready, cudaEventDisableTiming));
+  CK(cudaEventRecord(h->ev_ready, h->stream));
+  const int loops0 = h->sc_host->loops;
+  {
+    std::unique_lock<std::mutex> lk(b->mu);
+    b->waiting.push_back(&r);
+    b->cv.notify_all();
+    const auto t0 = std::chrono::steady_clock::now();
+    while (!r.done) {
+      const bool all_in = (int)b->waiting.size() >= b->active;
+      const bool waited = std::chrono::steady_clock::now() - t0 > std::chrono::microseconds(200);
+      if (!b->leading && !b->waiting.empty() && (all_in || waited)) {
+        b->leading = true;
+        std::vector<LoopReq*> take;
+        take.swap(b->waiting);
+        lk.unlock();
+        const int rc = launch_batch(b, take);
+        lk.lock();
+        for (LoopReq* q : take) {
+          q->rc = rc;
+          q->done = true;
+        }
+        b->leading = false;
+        b->cv.notify_all();
+      } else {
+        b->cv.wait_for(lk, std::chrono::microseconds(50));
+      }
+    }
+  }
+  if (r.rc != BEM_OK) return r.rc;
+  *solo = r.solo;
+  if (r.solo) return BEM_OK;
+  CKR(read_scalars(h));
+  const int ran = h->sc_host->loops - loops0 + 1;
+  h->launches += (unsigned long long)((ran + kLoopBody - 1) / kLoopBody) * kLoopBody * (pk ? 6 : 4);
+  if (!h->sc_host->done) return fail(BEM_ECUDA, "a batched CG loop stopped before the solve was done");
+  return BEM_OK;
+}
+
+// Under BEM_FLAG_TIME_PASSES every kTimeEvery-th chunk (the first of each
+// solve included) runs the graph with event-record nodes; the others run the
+// plain graph, so the sampling costs little of the time it measures.
+constexpr int kTimeEvery = 4;
+
+// Run chunks of the captured loop until the device sets `done` (or, batched
+// with other solves, the several-instance loop graph).
+int run_loop(bem_ctx* h, cudaGraphExec_t g, cudaGraphExec_t g_timed, int max_iter, bool pk, int es) {
+  // batched with other solves: rows of a multiple of 16 elements (the
+  // persistent row passes), no pass timing
+  if (h->batcher && !h->timing && loop_batchable(h)) {
+    bool solo = false;
+    const int rc = run_loop_batched(h, pk, es, &solo);
+    if (rc != BEM_OK || !solo) return rc;
+  }
+  const int max_launch = max_iter / kChunk + 2;
+  for (int l = 0; l < max_launch; ++l) {
+    const bool timed = h->timing && l % kTimeEvery == 0;
+    CK(cudaGraphLaunch(timed ? g_timed : g, h->stream));
+    h->launches += (unsigned long long)kChunk * (pk ? 6 : 4);
     CKR(read_scalars(h));
-    cudaEvent_t* ev = h->ev[pk ? 0 : 1];
-    for (int i = 0; i < 3; ++i) {
-      float ms = 0;
-      CK(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
-      h->pass_ms[i] += ms;
+    if (timed) {
+      cudaEvent_t* ev = h->ev[pk ? 0 : 1];
+      for (int i = 0; i < 3; ++i) {
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
+        h->pass_ms[i] += ms;
+      }
+      h->pass_count[0] += 1;
+      int rows = h->ny;
+      if (!pk) {
+        h->pass_count[1] += 1;
+        const int b0 = h->sc_host->band0, b1 = h->sc_host->band1;
+        rows = b1 >= b0 ? b1 - b0 + 1 : 0;
+      }
+      add_pass_work(h, pk, rows, es);
     }
-    h->pass_count[0] += 1;
-    int rows = h->ny;
-    if (!pk) {
-      h->pass_count[1] += 1;
-      const int b0 = h->sc_host->band0, b1 = h->sc_host->band1;
-      rows = b1 >= b0 ? b1 - b0 + 1 : 0;
-    }
-    add_pass_work(h, pk, rows, es);
     if (h->sc_host->done) return BEM_OK;
   }
-  const int loops0 = h->sc_host->loops;
-  CK(cudaGraphLaunch(g_loop, h->stream));
-  CKR(read_scalars(h));
-  const int ran = h->sc_host->loops - loops0 + 1;  // iterations started in the loop graph
-  h->launches += (unsigned long long)((ran + kLoopBody - 1) / kLoopBody) * kLoopBody * kpi;
-  if (!h->sc_host->done) return fail(BEM_ECUDA, "the device-driven CG loop stopped before the solve was done");
   return BEM_OK;
 }
 
@@ -586,12 +804,12 @@ int run_pk(bem_ctx* h, double d, double tol, int max_iter, bool warm, StepOut* s
     CKR(pick_sub(h, &sub));
     if (sub) return pk_in_box<T>(h, sub, d, tol, max_iter, warm, so);
   }
-  if (!pf.pk_graph[0]) CKR(capture_loop<T>(h, true, &pf.pk_graph[0]));
-  if (h->timing && !pf.pk_graph[1]) CKR(capture_timed<T>(h, true, &pf.pk_graph[1]));
+  if (!pf.pk_graph[0]) CKR(capture_chunk<T>(h, true, false, &pf.pk_graph[0]));
+  if (h->timing && !pf.pk_graph[1]) CKR(capture_chunk<T>(h, true, true, &pf.pk_graph[1]));
   launch_pk_init<T>(plan_of<T>(h), h->h64, d, pf.c, pf.p, pf.t, warm ? 1 : 0, h->ew_ngrid, h->stream);
   h->launches += 1;
   CKR(init_scalars(h, tol, max_iter, 0.0));
-  CKR(run_loop(h, pf.pk_graph[0], pf.pk_graph[1], true, (int)sizeof(T)));
+  CKR(run_loop(h, pf.pk_graph[0], pf.pk_graph[1], max_iter, true, (int)sizeof(T)));
   so->iterations += h->sc_host->iter;
   so->eps = h->sc_host->eps;
   if (h->sc_host->status != SC_OK) so->status = map_status(h->sc_host->status);
@@ -737,8 +955,8 @@ int run_fixed_cg(bem_ctx* h, double tol, int max_iter, double pcrit, StepOut* so
     CKR(pick_sub(h, &sub));
     if (sub) return fixed_cg_in_box<T>(h, sub, tol, max_iter, pcrit, so);
   }
-  if (!pf.cg_graph[0]) CKR(capture_loop<T>(h, false, &pf.cg_graph[0]));
-  if (h->timing && !pf.cg_graph[1]) CKR(capture_timed<T>(h, false, &pf.cg_graph[1]));
+  if (!pf.cg_graph[0]) CKR(capture_chunk<T>(h, false, false, &pf.cg_graph[0]));
+  if (h->timing && !pf.cg_graph[1]) CKR(capture_chunk<T>(h, false, true, &pf.cg_graph[1]));
   const size_t n = (size_t)h->nx * h->ny;
   launch_mask_field<T>(pf.p, h->S, n, h->stream);
   launch_mask_field<T>(pf.t, h->S, n, h->stream);
@@ -749,7 +967,7 @@ int run_fixed_cg(bem_ctx* h, double tol, int max_iter, double pcrit, StepOut* so
   launch_pass_c<T>(a, C_CG_G, h->stream);
   h->launches += 5;
   CKR(read_scalars(h));
-  if (!h->sc_host->done) CKR(run_loop(h, pf.cg_graph[0], pf.cg_graph[1], false, (int)sizeof(T)));
+  if (!h->sc_host->done) CKR(run_loop(h, pf.cg_graph[0], pf.cg_graph[1], max_iter, false, (int)sizeof(T)));
   so->iterations += h->sc_host->iter;
   so->eps = h->sc_host->eps;
   if (h->sc_host->status != SC_OK) so->status = map_status(h->sc_host->status);
@@ -1017,6 +1235,7 @@ static int create_ctx(int Nx, int Ny, double dx, double dy, double k, double nu,
     h->is_sub = true;
     h->own_stream = false;
     h->stream = parent->stream;
+    h->batcher = parent->batcher;
   } else if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
     return cleanup(fail(BEM_ECUDA, "stream creation failed"));
   }
@@ -1133,6 +1352,7 @@ extern "C" void bem_destroy(bem_handle h) {
   for (int i = 0; i < 2; ++i)
     for (int j = 0; j < 4; ++j)
       if (h->ev[i][j]) cudaEventDestroy(h->ev[i][j]);
+  if (h->ev_ready) cudaEventDestroy(h->ev_ready);
   fr(h->kq64); fr(h->geo); fr(h->tw64); fr(h->tw32); fr(h->khat64); fr(h->khat32); fr(h->W); fr(h->h64); fr(h->io64); fr(h->io64b);
   fr(h->S); fr(h->part); fr(h->partC); fr(h->partE); fr(h->stats); fr(h->sc);
   fr(h->f32.p); fr(h->f32.g); fr(h->f32.t); fr(h->f32.r); fr(h->f32.c);

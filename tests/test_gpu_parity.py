@@ -26,10 +26,19 @@ def torus_sizes(nx, ny):
 
 
 # ------------------------------------------------------------------ a1
-@pytest.mark.parametrize("nx,ny", [(16, 16), (24, 40), (64, 64), (7, 5)])
+@pytest.mark.parametrize("nx,ny,aspect", [(16, 16, 1), (24, 40, 1), (64, 64, 1), (7, 5, 1), (8, 40, 17),
+                                          (40, 8, 17)])
 @pytest.mark.parametrize("k", [-0.9, -0.5, 0.0, 0.3, 0.9])
-def test_influence_table(bem_mod, oracle_mod, cuda_ok, nx, ny, k):
+def test_influence_table(bem_mod, oracle_mod, cuda_ok, nx, ny, aspect, k):
+    # aspect > 1: elements `aspect` times longer in x (ny = 40) or in y (nx = 40).
+    # At k = 0.9 the oracle's adaptive cubature of the self-term of such an
+    # element, (a^2+b^2)^-0.95 over a 17:1 rectangle, does not converge (it
+    # returns inf), so that case is left out.
+    if aspect > 1 and k > 0.5:
+        pytest.skip("oracle cubature of a 17:1 self-term at k = 0.9 does not converge")
     dx, dy = 1.0 / nx, 1.0 / ny
+    if aspect > 1:
+        dx, dy = (aspect / 136.0, 1 / 136.0) if ny > nx else (1 / 136.0, aspect / 136.0)
     with bem_mod.Handle(nx, ny, dx, dy, k, 0.3) as h:
         Kg = h.influence_table()
     px, py = torus_sizes(nx, ny)

@@ -1,7 +1,10 @@
 """The request server (bem_server_*): each job's result is the same alone and
-in a mix of concurrent jobs, cached spectra are reused across materials,
-admission keeps the device bytes within the budget, and a failing job reports
-its status without stopping the others."""
+in a mix of concurrent jobs (within its precision's tolerance: jobs whose CG
+loops share a batched launch run the several-instance kernels, whose rounding
+may differ from the single-instance ones in the last bits; a job that runs
+alone in the server is bitwise its alone result), cached spectra are reused
+across materials, admission keeps the device bytes within the budget, and a
+failing job reports its status without stopping the others."""
 import numpy as np
 import pytest
 
@@ -90,6 +93,7 @@ def submit(srv, job):
 
 
 def assert_same(alone, comp):
+    """Bitwise the alone result."""
     res_a, p_a, rc_a, _ = alone
     assert comp["status"] == rc_a
     for ra, rb in zip(res_a, comp["results"]):
@@ -97,6 +101,23 @@ def assert_same(alone, comp):
         for f in FIELDS:
             assert ra[f] == rb[f] or (np.isnan(ra[f]) and np.isnan(rb[f])), f
     assert np.array_equal(p_a, comp["final_pressure"])
+
+
+# a result alone and in a batched mix: pressure and force within these of the
+# alone result (relative), contact counts exact
+MIX_TOL = {"fp64": 1e-10, "fp32_refine": 1e-9, "fp32": 1e-5}
+
+
+def assert_close(alone, comp, prec):
+    res_a, p_a, rc_a, _ = alone
+    tol = MIX_TOL[prec]
+    assert comp["status"] == rc_a
+    fmax = max(max(abs(r["force"]) for r in res_a), 1e-300)
+    for ra, rb in zip(res_a, comp["results"]):
+        assert ra["contact_count"] == rb.contact_count
+        assert abs(ra["force"] - rb.force) <= tol * fmax
+    nrm = np.linalg.norm(p_a)
+    assert np.linalg.norm(p_a - comp["final_pressure"]) <= tol * max(nrm, 1e-300)
 
 
 def test_alone_equals_mix(bem_mod, oracle_mod):
@@ -108,7 +129,7 @@ def test_alone_equals_mix(bem_mod, oracle_mod):
         assert srv.pending() == 0
     assert sorted(comps) == sorted(tags)
     for t, a, j in zip(tags, alone, jobs):
-        assert_same(a, comps[t])
+        assert_close(a, comps[t], j["precision"])
         assert comps[t]["device"] >= 0
         # and each served result is the oracle's, within its precision's tolerance
         assert_matches_oracle(oracle_mod, j, comps[t]["results"], comps[t]["final_pressure"])
@@ -206,3 +227,22 @@ def test_cancel_a_queued_job(bem_mod):
     assert comps[t_q]["status"] == bem_mod.BEM_ECANCELED
     assert (p == -7.0).all()
     assert comps[t_run]["status"] == bem_mod.BEM_OK
+
+
+def test_concurrent_loops_share_launches(bem_mod, oracle_mod):
+    """Eight jobs of one size class (128^2 paraboloids, each with its own k, so
+    each has its own handle) on eight workers: their CG loops run batched, one
+    launch per pass carrying several solves, every result equals the job's
+    alone result within its precision's tolerance, and one of them is also
+    checked against the oracle."""
+    jobs = [{"n": 128, "k": -0.7 + 0.2 * i, "nu": 0.3, "dgamma": 0.0, "adhesive": False,
+             "profile": "paraboloid", "seed": 0, "precision": "fp32_refine"} for i in range(8)]
+    alone = [run_alone(bem_mod, j) for j in jobs]
+    with bem_mod.Server(nworkers=8, hbm_budget_bytes=8 << 30) as srv:
+        tags = [submit(srv, j) for j in jobs]
+        comps = {c["tag"]: c for c in srv.drain()}
+        launches, loops = srv.loop_stats()
+    for t, a in zip(tags, alone):
+        assert_close(a, comps[t], "fp32_refine")
+    assert launches > 0 and loops >= 1.5 * launches, (launches, loops)
+    assert_matches_oracle(oracle_mod, jobs[3], comps[tags[3]]["results"], comps[tags[3]]["final_pressure"])
