@@ -126,7 +126,24 @@ struct PassArgs {
   Scalars* sc;
   unsigned int* kerr;   // sticky error word (may be null: errors then go unreported)
   int use_band;         // fixed-set CG loop: restrict the passes to rows sc->band0 .. band1
+  // Tensor map (device memory) of W as (M+1) rows of 2 rows_w reals with boxes
+  // of 2 nbA reals x w_box rows: the persistent pass C stages a row group's W
+  // columns with 2D TMA loads.  Null: 16-byte cp.async instead.
+  const void* tmW;
 };
+
+// Rows of W per box of the TMA staging, and rows of pass C's W staging area
+// (whole boxes: the last box of a long transform reads past row M, zero-filled).
+__host__ __device__ constexpr int w_box_rows(int M) { return M + 1 <= 256 ? M + 1 : 256; }
+__host__ __device__ constexpr int w_stage_rows(int M) {
+  return (M + 1 + w_box_rows(M) - 1) / w_box_rows(M) * w_box_rows(M);
+}
+// Dynamic shared memory of the persistent pass C: transform rows (128-byte
+// aligned end, the TMA destination follows) | W staging | epilogue staging.
+__host__ __device__ constexpr size_t pass_c_w_offset(size_t smemC) { return (smemC + 127) & ~(size_t)127; }
+__host__ __device__ constexpr size_t pass_c_smem(size_t smemC, int M, int nb, int cx_bytes, size_t epi_bytes) {
+  return pass_c_w_offset(smemC) + (((size_t)cx_bytes * w_stage_rows(M) * nb + 15) & ~(size_t)15) + epi_bytes;
+}
 
 template <typename T> void launch_pass_a(const PassArgs<T>& a, int mode, cudaStream_t s);
 template <typename T> void launch_pass_b(const PassArgs<T>& a, int mode, cudaStream_t s);

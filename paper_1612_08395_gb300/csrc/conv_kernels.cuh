@@ -341,7 +341,7 @@ __global__ void BEM_ROW_BOUNDS(LOGL) k_pass_a(PassArgs<T> a) {
   using F = FftC<T, LOGL>;
   constexpr int L = F::L, L8 = F::L8, M = L;
   constexpr bool HALF = MODE != A_TORUS;  // conv inputs fill the first half only
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ double red[3 * 32];
   Cx* sm = reinterpret_cast<Cx*>(smem_raw);
   Scalars* sc = a.sc;
@@ -507,7 +507,7 @@ __device__ __forceinline__ void pass_ap_body(const PassArgs<T>& a) {
   using Cx = C<T>;
   using F = FftC<T, LOGL>;
   constexpr int L = F::L, L8 = F::L8, M = L;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ double red[3 * 32];
   Cx* sm = reinterpret_cast<Cx*>(smem_raw);
   Scalars* sc = a.sc;
@@ -647,7 +647,7 @@ __device__ __forceinline__ void pass_b_body(const PassArgs<T>& a) {
   using F = FftC<T, LOGL>;
   constexpr int L = F::L, L8 = F::L8, R0 = F::R0, hyq = (L >> 1) + 1;
   constexpr bool HALF = MODE == B_CONV;  // Ny <= Py/2 rows in, Ny rows out
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   Cx* sm = reinterpret_cast<Cx*>(smem_raw);
   if (MODE == B_CONV && a.sc != nullptr) {
     if (a.sc->done) return;
@@ -961,7 +961,7 @@ __global__ void BEM_ROW_BOUNDS(LOGL) k_pass_c(PassArgs<T> a) {
   using Cx = C<T>;
   using F = FftC<T, LOGL>;
   constexpr int L = F::L, L8 = F::L8, M = L;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ double red[3 * 32];
   __shared__ int lastflag;
   Cx* sm = reinterpret_cast<Cx*>(smem_raw);
@@ -1123,7 +1123,7 @@ __device__ __forceinline__ void pass_cp_body(const PassArgs<T>& a) {
   using Cx = C<T>;
   using F = FftC<T, LOGL>;
   constexpr int L = F::L, L8 = F::L8, M = L;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ double red[3 * 32];
   __shared__ int lastflag;
   Cx* sm = reinterpret_cast<Cx*>(smem_raw);
@@ -1141,15 +1141,29 @@ __device__ __forceinline__ void pass_cp_body(const PassArgs<T>& a) {
   const Cx* tw = reinterpret_cast<const Cx*>(a.twA);
   const int* sp = a.spA;
   Cx* buf = sm + b * rs;
-  // shared memory: transform rows | W staging [(M+1) x nb] | epilogue staging
-  const size_t off_w = (sizeof(Cx) * (size_t)nb * rs + 15) & ~(size_t)15;
+  // shared memory: transform rows | W staging [w_stage_rows(M) x nb] | epilogue staging
+  const size_t off_w = pass_c_w_offset(sizeof(Cx) * (size_t)nb * rs);
   Cx* wst = reinterpret_cast<Cx*>(smem_raw + off_w);
-  const size_t off_e = off_w + ((sizeof(Cx) * (size_t)(M + 1) * nb + 15) & ~(size_t)15);
+  const size_t off_e = off_w + ((sizeof(Cx) * (size_t)w_stage_rows(M) * nb + 15) & ~(size_t)15);
   T* st = reinterpret_cast<T*>(smem_raw + off_e);
   uint8_t* ss = reinterpret_cast<uint8_t*>(st) + (size_t)EpiStage<MODE>::nT * sizeof(T) * nb * nx;
 
+  // W of a row group by TMA: thread 0 issues one 2D box load per w_box_rows(M)
+  // rows of W (nb complex values of each), completing on wbar
+  __shared__ unsigned long long wbar;
+  unsigned wphase = 0;
+  const bool tma = a.tmW != nullptr;
   auto prefetch_w = [&](int gg) {
     const int r0 = gg * nb, rows = min(nb, ny - r0);
+    if (tma) {
+      if (tid == 0) {
+        constexpr int bo = w_box_rows(M), nload = w_stage_rows(M) / bo;
+        fence_proxy_async_smem();
+        mbar_expect_tx(&wbar, (unsigned)(nload * bo * nb * (int)sizeof(Cx)));
+        for (int j = 0; j < nload; ++j) tma_load_2d(wst + (size_t)j * bo * nb, a.tmW, 2 * r0, j * bo, &wbar);
+      }
+      return;
+    }
     if (sizeof(Cx) == 8 && nb >= 2 && rows == nb && (a.rows_w & 1) == 0) {
       // FP32 and an even number of full rows: 16-byte chunks of two rows
       const int lh = lognb - 1;
@@ -1169,7 +1183,10 @@ __device__ __forceinline__ void pass_cp_body(const PassArgs<T>& a) {
   };
   // epilogue fields: thread 0 issues one bulk copy per field row, completing on ebar
   __shared__ unsigned long long ebar;
-  if (tid == 0) mbar_init(&ebar, 1);
+  if (tid == 0) {
+    mbar_init(&ebar, 1);
+    if (tma) mbar_init(&wbar, 1);
+  }
   __syncthreads();
   unsigned ephase = 0;
   auto prefetch_e = [&](int gg) {
@@ -1206,8 +1223,17 @@ __device__ __forceinline__ void pass_cp_body(const PassArgs<T>& a) {
   }
   for (; g < gend; g += gridDim.x) {
     const int row0 = g * nb;
-    cp_async_wait_all();  // W of this group
-    __syncthreads();
+    if (tma) {  // W of this group
+      const bool ok = mbar_wait(&wbar, wphase);
+      wphase ^= 1u;
+      if (__syncthreads_or(!ok)) {  // it never arrived: give up together
+        if (tid == 0 && a.kerr) atomicOr(a.kerr, 1u);
+        return;
+      }
+    } else {
+      cp_async_wait_all();  // W of this group
+      __syncthreads();
+    }
     // rebuild the packed half-length spectrum from the staged W rows
 #pragma unroll 2
     for (int idx = tid; idx < ((M >> 1) + 1) << lognb; idx += nthr) {
@@ -1622,9 +1648,8 @@ void launch_c_mode(const PassArgs<T>& a, cudaStream_t s) {
   const dim3 block(a.pl.threadsA);
   const int groups = a.pl.gridA;
   if (BEM_PERSISTENT && (a.pl.nx & 15) == 0 && epi_fields_aligned<T>(a)) {
-    const size_t smem = ((a.pl.smemC + 15) & ~(size_t)15) +
-                        ((sizeof(C<T>) * (size_t)(a.pl.M + 1) * a.pl.nbA + 15) & ~(size_t)15) +
-                        epi_stage_bytes<T, MODE>(a.pl.nbA, a.pl.nx);
+    const size_t smem = pass_c_smem(a.pl.smemC, a.pl.M, a.pl.nbA, (int)sizeof(C<T>),
+                                    epi_stage_bytes<T, MODE>(a.pl.nbA, a.pl.nx));
     switch (a.pl.gA.logL) {
 #define BEM_CASE(LG)                                                                        \
   case LG: {                                                                                \
@@ -1669,9 +1694,8 @@ template <typename T, int MODE>
 void launch_c_mode_mi(const PassArgs<T>& a0, const PassArgs<T>* arr, int n, cudaStream_t s) {
   const dim3 block(a0.pl.threadsA);
   const int groups = a0.pl.gridA;
-  const size_t smem = ((a0.pl.smemC + 15) & ~(size_t)15) +
-                      ((sizeof(C<T>) * (size_t)(a0.pl.M + 1) * a0.pl.nbA + 15) & ~(size_t)15) +
-                      epi_stage_bytes<T, MODE>(a0.pl.nbA, a0.pl.nx);
+  const size_t smem = pass_c_smem(a0.pl.smemC, a0.pl.M, a0.pl.nbA, (int)sizeof(C<T>),
+                                  epi_stage_bytes<T, MODE>(a0.pl.nbA, a0.pl.nx));
   switch (a0.pl.gA.logL) {
 #define BEM_CASE(LG)                                                                        \
   case LG: {                                                                                \

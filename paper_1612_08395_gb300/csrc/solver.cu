@@ -16,6 +16,8 @@
 #include <vector>
 #include <string>
 
+#include <cuda.h>  // CUtensorMap (the encoder comes from the driver entry point)
+
 #include "bem.h"
 #include "bem_impl.h"
 #include "geo_table.h"
@@ -138,7 +140,7 @@ bool shape_fits(const Plan& pl, int esize) {
   if (pl.threadsB < 64 || pl.threadsB > capB || (pl.threadsB & 31)) return false;
   const size_t lim = 200 * 1024, rows = (size_t)pl.nbA * pl.nx;
   if (pl.smemA + (3 * (size_t)esize + 1) * rows + 16 > lim) return false;
-  if (pl.smemC + (size_t)2 * esize * (pl.M + 1) * pl.nbA + (2 * (size_t)esize + 1) * rows + 32 > lim) return false;
+  if (pass_c_smem(pl.smemC, pl.M, pl.nbA, 2 * esize, (2 * (size_t)esize + 1) * rows) + 32 > lim) return false;
   if (pl.smemB > lim) return false;
   return true;
 }
@@ -238,6 +240,10 @@ struct bem_ctx {
   // CG loops join this batcher when set (concurrent solves of the server)
   bem::LoopBatcher* batcher = nullptr;
   cudaEvent_t ev_ready = nullptr;  // this context's work before its batched loop
+  // Tensor maps of W for pass C's TMA staging, [FP32, FP64] views with the
+  // plan's rows per CTA (device memory; null where TMA does not apply)
+  void* tmw[2] = {nullptr, nullptr};
+  bool tmw_ok[2] = {false, false};
 };
 
 static int create_ctx(int Nx, int Ny, double dx, double dy, double k, double nu, double E0, double c0,
@@ -283,6 +289,65 @@ int ensure_fields(bem_ctx* h) {
   return BEM_OK;
 }
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn tensor_map_encoder() {
+  static EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return (EncodeTiledFn) nullptr;
+    }
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+// The tensor map of W for pass C's TMA staging in precision es (4 or 8): W as
+// (M+1) rows of 2 ny reals, boxes of 2 nb reals x w_box_rows(M) rows, zero fill
+// past the ends.  TMA wants 16-byte strides and box rows, so FP32 needs an even
+// ny and an even nb; where that fails (or TMA is unavailable) the map stays off
+// and pass C stages W with cp.async.  BEM_TMA=0 switches it off.
+int update_w_map(bem_ctx* h, int es, int nb) {
+  const int i = es == 8 ? 1 : 0;
+  h->tmw_ok[i] = false;
+  static const bool on = [] {
+    const char* e = getenv("BEM_TMA");
+    return !(e && e[0] == '0');
+  }();
+  EncodeTiledFn enc = tensor_map_encoder();
+  if (!on || !enc) return BEM_OK;
+  if (es == 4 && ((h->ny & 1) || (nb & 1))) return BEM_OK;
+  const int M = h->px / 2;
+  CUtensorMap m;
+  const cuuint64_t dims[2] = {(cuuint64_t)2 * h->ny, (cuuint64_t)M + 1};
+  const cuuint64_t strides[1] = {(cuuint64_t)2 * h->ny * es};
+  const cuuint32_t box[2] = {(cuuint32_t)(2 * nb), (cuuint32_t)w_box_rows(M)};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(&m, es == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, h->W,
+                         dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return BEM_OK;  // not representable: stay on cp.async
+  if (!h->tmw[i]) {
+    if (cudaMalloc(&h->tmw[i], sizeof(CUtensorMap)) != cudaSuccess) {
+      cudaGetLastError();
+      h->tmw[i] = nullptr;
+      return BEM_OK;
+    }
+    h->bytes += sizeof(CUtensorMap);
+  }
+  // ordered before every later launch on the handle's stream
+  CK(cudaMemcpyAsync(h->tmw[i], &m, sizeof m, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->tmw_ok[i] = true;
+  return BEM_OK;
+}
+
 template <typename T>
 PassArgs<T> make_args(bem_ctx* h) {
   PassArgs<T> a{};
@@ -309,6 +374,7 @@ PassArgs<T> make_args(bem_ctx* h) {
   a.partA = h->part;
   a.partC = h->partC;
   a.partE = h->partE;
+  a.tmW = h->tmw_ok[sizeof(T) == 8 ? 1 : 0] ? h->tmw[sizeof(T) == 8 ? 1 : 0] : nullptr;
   a.sc = h->sc;
   a.kerr = &h->sc->kerr;
   return a;
@@ -1111,12 +1177,14 @@ struct ShapeKey {
 std::mutex g_tune_mu;
 std::map<ShapeKey, std::pair<int, int>> g_tuned;
 
-void set_plan32(bem_ctx* h, const Plan& pl) {
+int set_plan32(bem_ctx* h, const Plan& pl) {
   h->plan32 = pl;
+  CKR(update_w_map(h, 4, pl.nbA));
   int* g32 = h->geo;
   const int M = h->px / 2;
   launch_geo_tables(g32, g32 + kSoEntries, pl.gA, 4, h->stream);
   launch_geo_tables(g32 + kSoEntries + M, g32 + 2 * kSoEntries + M, pl.gB, 4, h->stream);
+  return BEM_OK;
 }
 
 // Device milliseconds of passes A, B, C (summed over `reps` plain transforms).
@@ -1160,7 +1228,7 @@ int autotune32(bem_ctx* h) {
   auto it = g_tuned.find(key);
   if (it != g_tuned.end()) {
     if (it->second.first != base.nbA || it->second.second != base.nbB)
-      set_plan32(h, plan_with(h->nx, h->ny, h->px, h->py, 4, base.nsm, it->second.first, it->second.second));
+      CKR(set_plan32(h, plan_with(h->nx, h->ny, h->px, h->py, 4, base.nsm, it->second.first, it->second.second)));
     return BEM_OK;
   }
   CKR(ensure_fields<float>(h));
@@ -1172,7 +1240,7 @@ int autotune32(bem_ctx* h) {
   for (int nb : {base.nbA / 2, base.nbA * 2}) {
     const Plan pl = plan_with(h->nx, h->ny, h->px, h->py, 4, base.nsm, nb, base.nbB);
     if (nb < 1 || !shape_fits(pl, 4)) continue;
-    set_plan32(h, pl);
+    CKR(set_plan32(h, pl));
     double t[3];
     CKR(time_passes32(h, reps, t));
     if (t[0] + t[2] < 0.97 * tAC) { tAC = t[0] + t[2]; bestA = nb; }
@@ -1180,12 +1248,12 @@ int autotune32(bem_ctx* h) {
   for (int nb : {base.nbB / 2, base.nbB * 2}) {
     const Plan pl = plan_with(h->nx, h->ny, h->px, h->py, 4, base.nsm, base.nbA, nb);
     if (nb < 1 || !shape_fits(pl, 4)) continue;
-    set_plan32(h, pl);
+    CKR(set_plan32(h, pl));
     double t[3];
     CKR(time_passes32(h, reps, t));
     if (t[1] < 0.97 * tB) { tB = t[1]; bestB = nb; }
   }
-  set_plan32(h, plan_with(h->nx, h->ny, h->px, h->py, 4, base.nsm, bestA, bestB));
+  CKR(set_plan32(h, plan_with(h->nx, h->ny, h->px, h->py, 4, base.nsm, bestA, bestB)));
   CK(cudaStreamSynchronize(h->stream));
   g_tuned[key] = {bestA, bestB};
   return BEM_OK;
@@ -1335,6 +1403,7 @@ static int create_ctx(int Nx, int Ny, double dx, double dy, double k, double nu,
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cleanup(fail(BEM_ECUDA, "set-up kernels failed: %s", cudaGetErrorString(e)));
+  if ((rc = update_w_map(h, 4, h->plan32.nbA)) || (rc = update_w_map(h, 8, h->plan64.nbA))) return cleanup(rc);
   if ((rc = autotune32(h))) return cleanup(rc);
   *out = h;
   return BEM_OK;
@@ -1353,6 +1422,7 @@ extern "C" void bem_destroy(bem_handle h) {
     for (int j = 0; j < 4; ++j)
       if (h->ev[i][j]) cudaEventDestroy(h->ev[i][j]);
   if (h->ev_ready) cudaEventDestroy(h->ev_ready);
+  fr(h->tmw[0]); fr(h->tmw[1]);
   fr(h->kq64); fr(h->geo); fr(h->tw64); fr(h->tw32); fr(h->khat64); fr(h->khat32); fr(h->W); fr(h->h64); fr(h->io64); fr(h->io64b);
   fr(h->S); fr(h->part); fr(h->partC); fr(h->partE); fr(h->stats); fr(h->sc);
   fr(h->f32.p); fr(h->f32.g); fr(h->f32.t); fr(h->f32.r); fr(h->f32.c);
