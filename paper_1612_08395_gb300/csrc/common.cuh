@@ -376,18 +376,123 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 }
 
 // Signal that this block's partials are written; returns true in every thread
-// of the block that arrives last.  The counter is reset by that block.
+// of the block that arrives last.  The counter is reset by that block.  Only
+// thread 0 writes a block's partials, so only it fences: release before its
+// arrival, and, in the last block, acquire before the partials are read (with
+// L2 loads, after the barrier that publishes the flag).
 __device__ __forceinline__ bool last_block_arrival(unsigned int* counter, int* flag_smem) {
-  __threadfence();
-  __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned int t = atomicAdd(counter, 1u);
-    *flag_smem = (t == gridDim.x - 1) ? 1 : 0;
+    __threadfence();
+    const unsigned int t = atomicAdd(counter, 1u);
+    const bool last = t == gridDim.x - 1;
+    if (last) __threadfence();
+    *flag_smem = last ? 1 : 0;
   }
   __syncthreads();
-  bool last = *flag_smem != 0;
-  if (last) __threadfence();
-  return last;
+  return *flag_smem != 0;
+}
+
+// ---------------------------------------------------------------------------
+// Float-float sums for the FP32 path.  GB300 executes FP64 at a small fraction
+// of its FP32 rate (about two FP64 operations per clock and SM), so a
+// block-wide FP64 shuffle reduction costs over a microsecond per CTA.  The FP32
+// path's per-thread values are FP32; their block and grid sums are formed as
+// unevaluated pairs hi + lo of floats instead, with Knuth's error-free TwoSum
+// for the leading parts (about 44 significant bits, far beyond the inputs), in
+// the same fixed order as block_sum, and turned into FP64 once at the end.
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+  const float s = a.x + b.x;
+  const float v = s - a.x;
+  float e = (a.x - (s - v)) + (b.x - v);  // a.x + b.x = s + e exactly
+  e += a.y + b.y;
+  const float hi = s + e;
+  return make_float2(hi, e - (hi - s));
+}
+__device__ __forceinline__ float2 ff_shfl_down(float2 x, int o) {
+  return make_float2(__shfl_down_sync(0xffffffffu, x.x, o), __shfl_down_sync(0xffffffffu, x.y, o));
+}
+__device__ __forceinline__ double ff_to_double(float2 v) { return (double)v.x + (double)v.y; }
+
+// Block reduction of NQ float-float values; result valid in thread 0.  `red`
+// must hold NQ * (blockDim.x/32) float2 of shared memory.
+template <int NQ>
+__device__ __forceinline__ void block_sum_ff(float2 (&v)[NQ], float2* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    float2 x = v[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = ff_add(x, ff_shfl_down(x, o));
+    v[q] = x;
+  }
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) red[q * nw + wid] = v[q];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      float2 x = lane < nw ? red[q * nw + lane] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x = ff_add(x, ff_shfl_down(x, o));
+      v[q] = x;
+    }
+  }
+  __syncthreads();
+}
+
+// This CTA's partial sums of the per-thread values acc[0 .. NQ-1] into its
+// slot pp (4 doubles).  FP32: float-float pairs (hi, lo) stored in the slot's
+// doubles; FP64: doubles.  Read back with grid_sum.
+template <typename T, int NQ>
+__device__ __forceinline__ void block_partials(const T* acc, double* pp, double* red) {
+  if constexpr (sizeof(T) == 4) {
+    float2 v[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) v[q] = make_float2((float)acc[q], 0.f);
+    block_sum_ff<NQ>(v, reinterpret_cast<float2*>(red));
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) reinterpret_cast<float2*>(pp)[q] = v[q];
+    }
+  } else {
+    double v[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) v[q] = (double)acc[q];
+    block_sum<NQ>(v, red);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) pp[q] = v[q];
+    }
+  }
+}
+
+// Sum of the partials that n CTAs wrote with block_partials<T, NQ>, in a fixed
+// order (deterministic); result in thread 0, as FP64.
+template <typename T, int NQ>
+__device__ __forceinline__ void grid_sum(const double* part, int n, double (&s)[NQ], double* red) {
+  if constexpr (sizeof(T) == 4) {
+    float2 v[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) v[q] = make_float2(0.f, 0.f);
+    for (int b = threadIdx.x; b < n; b += blockDim.x) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) v[q] = ff_add(v[q], __ldcg(reinterpret_cast<const float2*>(part + 4 * b + q)));
+    }
+    block_sum_ff<NQ>(v, reinterpret_cast<float2*>(red));
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) s[q] = ff_to_double(v[q]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) s[q] = 0.0;
+    for (int b = threadIdx.x; b < n; b += blockDim.x) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) s[q] += __ldcg(part + 4 * b + q);
+    }
+    block_sum<NQ>(s, red);
+  }
 }
 
 }  // namespace bem

@@ -42,18 +42,6 @@ template <typename T> __device__ __forceinline__ T tabs(T x) { return x < (T)0 ?
 // Iterations without halving the best eps before a CG solve is declared stalled.
 constexpr int kStall = 200;
 
-// Sum per-CTA partials in a fixed order (deterministic); result in thread 0.
-template <int NQ>
-__device__ __forceinline__ void sum_partials(const double* part, int n, double (&v)[NQ], double* red) {
-#pragma unroll
-  for (int q = 0; q < NQ; ++q) v[q] = 0.0;
-  for (int b = threadIdx.x; b < n; b += blockDim.x) {
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) v[q] += __ldcg(part + 4 * b + q);
-  }
-  block_sum<NQ>(v, red);
-}
-
 // Compile-time description of a length-2^LOGL transform for element type T.
 template <typename T, int LOGL>
 struct FftC {
@@ -415,14 +403,7 @@ __global__ void BEM_ROW_BOUNDS(LOGL) k_pass_a(PassArgs<T> a) {
     F::dif(buf, t, ls, tw);
     __syncthreads();
   }
-  if (MODE == A_PK_P) {
-    double vv[3] = {(double)acc[0], (double)acc[1], (double)acc[2]};
-    block_sum<3>(vv, red);
-    if (tid == 0) {
-      double* pp = a.partA + 4 * blockIdx.x;
-      pp[0] = vv[0]; pp[1] = vv[1]; pp[2] = vv[2];
-    }
-  }
+  if (MODE == A_PK_P) block_partials<T, 3>(acc, a.partA + 4 * blockIdx.x, red);
   // split the packed transform into the half spectrum, store transposed
   split_store<T, M>(sm, rs, nb, lognb, row0, nrows, a.spA, reinterpret_cast<const Cx*>(a.twS),
                     reinterpret_cast<Cx*>(a.W), a.rows_w, a.kerr);
@@ -613,14 +594,7 @@ __device__ __forceinline__ void pass_ap_body(const PassArgs<T>& a) {
     }
     split_store<T, M>(sm, rs, nb, lognb, row0, nrows, sp, tws, W, a.rows_w, a.kerr);
   }
-  if (MODE == A_PK_P) {
-    double vv[3] = {(double)acc[0], (double)acc[1], (double)acc[2]};
-    block_sum<3>(vv, red);
-    if (tid == 0) {
-      double* pp = a.partA + 4 * blockIdx.x;
-      pp[0] = vv[0]; pp[1] = vv[1]; pp[2] = vv[2];
-    }
-  }
+  if (MODE == A_PK_P) block_partials<T, 3>(acc, a.partA + 4 * blockIdx.x, red);
 }
 
 // One launch of the persistent pass A; and the same over several instances of
@@ -1098,17 +1072,12 @@ __global__ void BEM_ROW_BOUNDS(LOGL) k_pass_c(PassArgs<T> a) {
         epi_apply<T, MODE>(a, rowoff + 2 * n + h, us * (h ? v[e].y : v[e].x), ein[e][h], acc);
   }
   if (MODE == C_PLAIN || MODE == C_GAP) return;
-  double vv[2] = {(double)acc[0], (double)acc[1]};
-  block_sum<2>(vv, red);
-  if (tid == 0) {
-    double* pp = a.partC + 4 * blockIdx.x;
-    pp[0] = vv[0]; pp[1] = vv[1];
-  }
+  block_partials<T, 2>(acc, a.partC + 4 * blockIdx.x, red);
   if (!last_block_arrival(MODE == C_PK_G ? &sc->cnt_c : &sc->cnt_a, &lastflag)) return;
   double s2[2];
-  sum_partials<2>(a.partC, gridDim.x, s2, red);
+  grid_sum<T, 2>(a.partC, gridDim.x, s2, red);
   double s3[3] = {0, 0, 0};
-  if (MODE == C_PK_G) sum_partials<3>(a.partA, __ldcg(&sc->nA), s3, red);
+  if (MODE == C_PK_G) grid_sum<T, 3>(a.partA, __ldcg(&sc->nA), s3, red);
   if (tid != 0) return;
   pass_c_finalize<MODE>(sc, s2, s3);
 }
@@ -1311,17 +1280,12 @@ __device__ __forceinline__ void pass_cp_body(const PassArgs<T>& a) {
   }
   cp_async_wait_all();
   if (MODE == C_PLAIN || MODE == C_GAP) return;
-  double vv[2] = {(double)acc[0], (double)acc[1]};
-  block_sum<2>(vv, red);
-  if (tid == 0) {
-    double* pp = a.partC + 4 * blockIdx.x;
-    pp[0] = vv[0]; pp[1] = vv[1];
-  }
+  block_partials<T, 2>(acc, a.partC + 4 * blockIdx.x, red);
   if (!last_block_arrival(MODE == C_PK_G ? &sc->cnt_c : &sc->cnt_a, &lastflag)) return;
   double s2[2];
-  sum_partials<2>(a.partC, gridDim.x, s2, red);
+  grid_sum<T, 2>(a.partC, gridDim.x, s2, red);
   double s3[3] = {0, 0, 0};
-  if (MODE == C_PK_G) sum_partials<3>(a.partA, __ldcg(&sc->nA), s3, red);
+  if (MODE == C_PK_G) grid_sum<T, 3>(a.partA, __ldcg(&sc->nA), s3, red);
   if (tid != 0) return;
   pass_c_finalize<MODE>(sc, s2, s3);
 }
@@ -1419,12 +1383,10 @@ __device__ __forceinline__ void cg_update_body(int nx, const Fields<T>& f, doubl
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
       acc += cg_update_one<T>(p, g, t, r, i, tau);
   }
-  double v[1] = {(double)acc};
-  block_sum<1>(v, red);
-  if (threadIdx.x == 0) part[4 * blockIdx.x] = v[0];
+  block_partials<T, 1>(&acc, part + 4 * blockIdx.x, red);
   if (!last_block_arrival(&sc->cnt_e, &lastflag)) return;
   double s[1];
-  sum_partials<1>(part, gridDim.x, s, red);
+  grid_sum<T, 1>(part, gridDim.x, s, red);
   if (threadIdx.x != 0) return;
   sc->cnt_e = 0;
   const double Gn = s[0];
@@ -1480,7 +1442,7 @@ __global__ void k_detach(int n, Fields<T> f, double* part, Scalars* sc) {
   if (threadIdx.x == 0) { part[4 * blockIdx.x] = v[0]; part[4 * blockIdx.x + 1] = v[1]; }
   if (!last_block_arrival(&sc->cnt_r, &lastflag)) return;
   double s[2];
-  sum_partials<2>(part, gridDim.x, s, red);
+  grid_sum<double, 2>(part, gridDim.x, s, red);
   if (threadIdx.x != 0) return;
   sc->cnt_r = 0;
   sc->n_ol = s[0];
