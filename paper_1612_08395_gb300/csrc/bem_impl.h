@@ -48,6 +48,7 @@ struct Scalars {
   double tol;        // stopping tolerance
   double tau, beta, delta, G, G_old, eps, bnorm, pcrit;
   double sum_p, sum_dp, n_ol, n_ic, str, eps_min;
+  double stop2;      // fixed-set CG: stop once |g|^2 <= stop2 = (tol |b|)^2
   int max_iter, iter, done, status, have_tau, it_min;
   int nA;        // CTAs of the last pass A launch (its partials feed pass C)
   // Debug builds only: 1 = the first persistent pass A launch of the solve
@@ -60,7 +61,7 @@ struct Scalars {
   // CG iterations counted on the device, and the cap after which the solve
   // stops unconverged (the bound of the batched while-loop graph).
   int loops, max_loops;
-  unsigned int cnt_a, cnt_c, cnt_e, cnt_r;  // last-block arrival counters
+  unsigned int cnt_a, cnt_c, cnt_r;  // last-block arrival counters
   // Sticky device error bits (kept across solves: init_scalars does not copy
   // this member); 1 = a kernel gave up waiting for its own asynchronous copies,
   // 2 = a bounds check of a debug build (-DBEM_DEBUG_CHECKS) failed.
@@ -74,7 +75,7 @@ enum PassAMode {
   A_PLAIN = 0,  // x = src
   A_PK_P = 1,   // Polonsky-Keer update of p (steps 7-8), partials sum|dp|, sum p, #overlap
   A_PK_T = 2,   // t = (p > 0) ? g + beta t : 0
-  A_CG_T = 3,   // t = S ? g + beta t : 0
+  A_CG_T = 3,   // fixed-set CG: p -= tau t, g -= tau r (the previous step, if any), t = S ? g + beta t : 0
   A_TORUS = 4   // x = K on the even torus (spectrum set-up, FP64)
 };
 // Pass C (row complex-to-real FFT) epilogue modes.
@@ -82,7 +83,7 @@ enum PassCMode {
   C_PLAIN = 0,  // dst = u
   C_PK_G = 1,   // g = u + c; partial sum_{p>0} g^2, #(p>0); last block: eps, delta, beta
   C_PK_R = 2,   // partials sum_{p>0} g t, sum_{p>0} r t; last block: tau
-  C_CG_R = 3,   // r = S ? u : 0 (stored); partial sum t r; last block: tau
+  C_CG_R = 3,   // r = S ? u : 0 (stored); partials t.r, g.r, r.r, g.g; last block: stop test, tau, beta
   C_CG_G = 4,   // g = S ? u + c : 0; partials sum g^2, sum_S c^2; last block: G, bnorm
   C_GAP = 5     // g = u + c (no mask) -- FP64 residual of the refinement
 };
@@ -122,7 +123,6 @@ struct PassArgs {
   double uscale;        // pass C: A / (Px Py)
   double* partA;        // per-CTA partials, 4 per CTA
   double* partC;
-  double* partE;        // per-CTA partials of the CG update (several-instance launches)
   Scalars* sc;
   unsigned int* kerr;   // sticky error word (may be null: errors then go unreported)
   int use_band;         // fixed-set CG loop: restrict the passes to rows sc->band0 .. band1
@@ -158,7 +158,6 @@ template <typename T> void launch_pass_a_mi(const PassArgs<T>& a0, int mode, con
 template <typename T> void launch_pass_b_mi(const PassArgs<T>& a0, const PassArgs<T>* arr, int n, cudaStream_t s);
 template <typename T> void launch_pass_c_mi(const PassArgs<T>& a0, int mode, const PassArgs<T>* arr, int n,
                                             cudaStream_t s);
-template <typename T> void launch_cg_update_mi(const PassArgs<T>* arr, int n, int ngrid, cudaStream_t s);
 // Sets the while-loop condition `cond` to "some instance is not done".
 template <typename T> void launch_batch_ctl(const PassArgs<T>* arr, int n, unsigned long long cond, cudaStream_t s);
 
@@ -173,8 +172,9 @@ int tc_column_pass_setup();  // once per device, when enabled
 // Elementwise kernels.
 template <typename T> void launch_pk_init(const Plan& pl, const double* h64, double d, T* c, T* p,
                                           T* t, int warm, int ngrid, cudaStream_t s);
-template <typename T> void launch_cg_update(const Plan& pl, Fields<T> f, double* part, Scalars* sc,
-                                            int ngrid, cudaStream_t s);
+// The pending last update of a fixed-set CG solve (if pass C left one).
+template <typename T> void launch_cg_finish(const Plan& pl, Fields<T> f, const Scalars* sc, int ngrid,
+                                            cudaStream_t s);
 void launch_box(const Plan& pl, const uint8_t* S, Scalars* sc, cudaStream_t s);
 void launch_box_overlap(const Plan& pl, const double* h, double d, Scalars* sc, cudaStream_t s);
 void launch_box_copy64(const double* src, int nx, int ny, int x0, int y0, double* dst, int bx, int by,

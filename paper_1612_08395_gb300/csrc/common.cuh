@@ -274,11 +274,9 @@ template <int NQ>
 __device__ __forceinline__ void block_sum(double (&v)[NQ], double* red) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) {
-    double x = v[q];
+  for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    v[q] = x;
+    for (int q = 0; q < NQ; ++q) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
   }
   __syncthreads();
   if (lane == 0) {
@@ -288,11 +286,11 @@ __device__ __forceinline__ void block_sum(double (&v)[NQ], double* red) {
   __syncthreads();
   if (wid == 0) {
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-      double x = lane < nw ? red[q * nw + lane] : 0.0;
+    for (int q = 0; q < NQ; ++q) v[q] = lane < nw ? red[q * nw + lane] : 0.0;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-      v[q] = x;
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
     }
   }
   __syncthreads();
@@ -418,12 +416,11 @@ __device__ __forceinline__ double ff_to_double(float2 v) { return (double)v.x + 
 template <int NQ>
 __device__ __forceinline__ void block_sum_ff(float2 (&v)[NQ], float2* red) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // the NQ sums advance level by level together (independent chains)
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) {
-    float2 x = v[q];
+  for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x = ff_add(x, ff_shfl_down(x, o));
-    v[q] = x;
+    for (int q = 0; q < NQ; ++q) v[q] = ff_add(v[q], ff_shfl_down(v[q], o));
   }
   __syncthreads();
   if (lane == 0) {
@@ -433,11 +430,11 @@ __device__ __forceinline__ void block_sum_ff(float2 (&v)[NQ], float2* red) {
   __syncthreads();
   if (wid == 0) {
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-      float2 x = lane < nw ? red[q * nw + lane] : make_float2(0.f, 0.f);
+    for (int q = 0; q < NQ; ++q) v[q] = lane < nw ? red[q * nw + lane] : make_float2(0.f, 0.f);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x = ff_add(x, ff_shfl_down(x, o));
-      v[q] = x;
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) v[q] = ff_add(v[q], ff_shfl_down(v[q], o));
     }
   }
   __syncthreads();
@@ -472,26 +469,35 @@ __device__ __forceinline__ void block_partials(const T* acc, double* pp, double*
 // Sum of the partials that n CTAs wrote with block_partials<T, NQ>, in a fixed
 // order (deterministic); result in thread 0, as FP64.
 template <typename T, int NQ>
-__device__ __forceinline__ void grid_sum(const double* part, int n, double (&s)[NQ], double* red) {
+__device__ __forceinline__ void grid_sum(const double* part, int n, double* s, double* red) {
   if constexpr (sizeof(T) == 4) {
     float2 v[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) v[q] = make_float2(0.f, 0.f);
     for (int b = threadIdx.x; b < n; b += blockDim.x) {
+      float2 x[NQ];  // all loads in flight before the first use
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) v[q] = ff_add(v[q], __ldcg(reinterpret_cast<const float2*>(part + 4 * b + q)));
+      for (int q = 0; q < NQ; ++q) x[q] = __ldcg(reinterpret_cast<const float2*>(part + 4 * b + q));
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) v[q] = ff_add(v[q], x[q]);
     }
     block_sum_ff<NQ>(v, reinterpret_cast<float2*>(red));
 #pragma unroll
     for (int q = 0; q < NQ; ++q) s[q] = ff_to_double(v[q]);
   } else {
+    double v[NQ];
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) s[q] = 0.0;
+    for (int q = 0; q < NQ; ++q) v[q] = 0.0;
     for (int b = threadIdx.x; b < n; b += blockDim.x) {
+      double x[NQ];
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) s[q] += __ldcg(part + 4 * b + q);
+      for (int q = 0; q < NQ; ++q) x[q] = __ldcg(part + 4 * b + q);
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) v[q] += x[q];
     }
-    block_sum<NQ>(s, red);
+    block_sum<NQ>(v, red);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) s[q] = v[q];
   }
 }
 

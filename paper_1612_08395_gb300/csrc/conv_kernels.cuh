@@ -140,7 +140,7 @@ struct FftC {
 // compute the transform input (with the CG work of the mode) and store.
 template <typename T>
 struct PIn {
-  T p, t, g;
+  T p, t, g, r;
   uint8_t s;
 };
 
@@ -153,7 +153,7 @@ __device__ __forceinline__ void pro_gather(const PassArgs<T>& a, size_t i, PIn<T
   } else if (MODE == A_PK_T) {
     x.p = a.f.p[i]; x.t = a.f.t[i]; x.g = a.f.g[i];
   } else if (MODE == A_CG_T) {
-    x.s = a.f.S[i]; x.t = a.f.t[i]; x.g = a.f.g[i];
+    x.s = a.f.S[i]; x.t = a.f.t[i]; x.g = a.f.g[i]; x.p = a.f.p[i]; x.r = a.f.r[i];
   }
 }
 
@@ -173,7 +173,7 @@ __device__ __forceinline__ T* pro_out(const PassArgs<T>& a) {
 // Transform input of one element with the CG work of the mode (the value the
 // mode also stores back into pro_out), without the store.
 template <typename T, int MODE>
-__device__ __forceinline__ T pro_value(const PIn<T>& x, bool upd, T tau, T beta, T* acc) {
+__device__ __forceinline__ T pro_value(PIn<T>& x, bool upd, T tau, T beta, T* acc) {
   if (MODE == A_PLAIN) {
     return x.p;
   } else if (MODE == A_PK_P) {
@@ -190,7 +190,11 @@ __device__ __forceinline__ T pro_value(const PIn<T>& x, bool upd, T tau, T beta,
     return q;
   } else if (MODE == A_PK_T) {
     return x.p > (T)0 ? x.g + beta * x.t : (T)0;
-  } else {  // A_CG_T
+  } else {  // A_CG_T: the previous iteration's update, then the new direction
+    if (upd) {
+      x.p -= tau * x.t;
+      x.g -= tau * x.r;
+    }
     return x.s ? x.g + beta * x.t : (T)0;
   }
 }
@@ -219,8 +223,14 @@ __device__ __forceinline__ T pro_apply(const PassArgs<T>& a, size_t i, const PIn
     const T tv = x.p > (T)0 ? x.g + beta * x.t : (T)0;
     a.f.t[i] = tv;
     return tv;
-  } else {  // A_CG_T
-    const T tv = x.s ? x.g + beta * x.t : (T)0;
+  } else {  // A_CG_T: the previous iteration's update, then the new direction
+    T gv = x.g;
+    if (upd) {
+      a.f.p[i] = x.p - tau * x.t;
+      gv = x.g - tau * x.r;
+      a.f.g[i] = gv;
+    }
+    const T tv = x.s ? gv + beta * x.t : (T)0;
     a.f.t[i] = tv;
     return tv;
   }
@@ -349,7 +359,7 @@ __global__ void BEM_ROW_BOUNDS(LOGL) k_pass_a(PassArgs<T> a) {
   T acc[3] = {0, 0, 0};
   bool upd = false;
   T tau = 0, beta = 0;
-  if (MODE == A_PK_P) { upd = sc->have_tau != 0; tau = (T)sc->tau; }
+  if (MODE == A_PK_P || MODE == A_CG_T) { upd = sc->have_tau != 0; tau = (T)sc->tau; }
   if (MODE == A_PK_T || MODE == A_CG_T) beta = (T)sc->beta;
   if (MODE == A_PK_P && blockIdx.x == 0 && tid == 0) sc->nA = gridDim.x;
   const size_t rowoff = (size_t)row * ncols;
@@ -415,7 +425,7 @@ __global__ void BEM_ROW_BOUNDS(LOGL) k_pass_a(PassArgs<T> a) {
 // shared memory as bulk copies (one per field row).  Used when rows are
 // multiples of 16 elements and the fields are 16-byte aligned.
 template <int MODE> struct ProStage {
-  static constexpr int nT = (MODE == A_PK_P || MODE == A_PK_T) ? 3 : (MODE == A_CG_T ? 2 : (MODE == A_PLAIN ? 1 : 0));
+  static constexpr int nT = (MODE == A_PK_P || MODE == A_PK_T) ? 3 : (MODE == A_CG_T ? 4 : (MODE == A_PLAIN ? 1 : 0));
   static constexpr bool S = MODE == A_CG_T;
 };
 template <typename T, int MODE>
@@ -425,7 +435,7 @@ __host__ __device__ constexpr size_t pro_stage_bytes(int nb, int nx) {
 template <typename T, int MODE>
 __device__ __forceinline__ const T* pro_field(const PassArgs<T>& a, int f) {
   if (MODE == A_PLAIN) return a.f.src;
-  if (MODE == A_CG_T) return f == 0 ? a.f.t : a.f.g;
+  if (MODE == A_CG_T) return f == 0 ? a.f.t : (f == 1 ? a.f.g : (f == 2 ? a.f.p : a.f.r));
   return f == 0 ? a.f.p : (f == 1 ? a.f.t : a.f.g);
 }
 // Thread 0 stages the prologue fields of rows row0 .. row0+rows-1 into shared
@@ -460,9 +470,10 @@ __device__ __forceinline__ void pro_gather_pair_staged(const T* st, const uint8_
     const V2<T> v = s2[0];
     x0.p = v.x; x1.p = v.y;
   } else if (MODE == A_CG_T) {
-    const V2<T> vt = s2[0], vg = s2[p2];
+    const V2<T> vt = s2[0], vg = s2[p2], vp = s2[2 * p2], vr = s2[3 * p2];
     const uchar2 vs = *reinterpret_cast<const uchar2*>(ss + j);
     x0.t = vt.x; x1.t = vt.y; x0.g = vg.x; x1.g = vg.y; x0.s = vs.x; x1.s = vs.y;
+    x0.p = vp.x; x1.p = vp.y; x0.r = vr.x; x1.r = vr.y;
   } else {
     const V2<T> vp = s2[0], vt = s2[p2], vg = s2[2 * p2];
     x0.p = vp.x; x1.p = vp.y; x0.t = vt.x; x1.t = vt.y; x0.g = vg.x; x1.g = vg.y;
@@ -474,7 +485,9 @@ __device__ __forceinline__ void pro_gather_staged(const T* st, const uint8_t* ss
                                                   int nb, PIn<T>& x) {
   const size_t j = (size_t)b * nx + col, plane = (size_t)nb * nx;
   if (MODE == A_PLAIN) { x.p = st[j]; }
-  else if (MODE == A_CG_T) { x.t = st[j]; x.g = st[plane + j]; x.s = ss[j]; }
+  else if (MODE == A_CG_T) {
+    x.t = st[j]; x.g = st[plane + j]; x.p = st[2 * plane + j]; x.r = st[3 * plane + j]; x.s = ss[j];
+  }
   else { x.p = st[j]; x.t = st[plane + j]; x.g = st[2 * plane + j]; }
 }
 
@@ -511,7 +524,7 @@ __device__ __forceinline__ void pass_ap_body(const PassArgs<T>& a) {
   T acc[3] = {0, 0, 0};
   bool upd = false;
   T tau = 0, beta = 0;
-  if (MODE == A_PK_P) { upd = sc->have_tau != 0; tau = (T)sc->tau; }
+  if (MODE == A_PK_P || MODE == A_CG_T) { upd = sc->have_tau != 0; tau = (T)sc->tau; }
   if (MODE == A_PK_T || MODE == A_CG_T) beta = (T)sc->beta;
   if (MODE == A_PK_P && blockIdx.x == 0 && tid == 0) sc->nA = gridDim.x;
 
@@ -579,6 +592,13 @@ __device__ __forceinline__ void pass_ap_body(const PassArgs<T>& a) {
           V2<T> o;
           o.x = x0; o.y = x1;
           *reinterpret_cast<V2<T>*>(out + rowoff + 2 * n) = o;
+        }
+        if (MODE == A_CG_T && upd) {  // p and g after the previous iteration's update
+          V2<T> o;
+          o.x = in[e][0].p; o.y = in[e][1].p;
+          *reinterpret_cast<V2<T>*>(a.f.p + rowoff + 2 * n) = o;
+          o.x = in[e][0].g; o.y = in[e][1].g;
+          *reinterpret_cast<V2<T>*>(a.f.g + rowoff + 2 * n) = o;
         }
         v[e] = mk<T>(x0, x1);
       }
@@ -726,7 +746,7 @@ __global__ void BEM_COL_BOUNDS(LOGL) k_pass_b_mi(const PassArgs<T>* __restrict__
 // start (their loads then overlap the inverse transform): number of T-typed
 // fields and whether the contact set S (one byte per element) is staged.
 template <int MODE> struct EpiStage {
-  static constexpr int nT = MODE == C_PK_G ? 2 : (MODE == C_CG_R || MODE == C_CG_G || MODE == C_GAP) ? 1 : 0;
+  static constexpr int nT = (MODE == C_PK_G || MODE == C_CG_R) ? 2 : (MODE == C_CG_G || MODE == C_GAP) ? 1 : 0;
   static constexpr bool S = MODE == C_CG_R || MODE == C_CG_G;
   static constexpr bool any = nT > 0 || S;
 };
@@ -751,7 +771,7 @@ __device__ __forceinline__ void epi_gather(const PassArgs<T>& a, size_t i, EIn<T
   } else if (MODE == C_PK_R) {
     x.p = a.f.p[i]; x.t = a.f.t[i]; x.g = a.f.g[i];
   } else if (MODE == C_CG_R) {
-    x.s = a.f.S[i]; x.t = a.f.t[i];
+    x.s = a.f.S[i]; x.t = a.f.t[i]; x.g = a.f.g[i];
   } else if (MODE == C_CG_G) {
     x.s = a.f.S[i]; x.c = a.f.c[i];
   } else if (MODE == C_GAP) {
@@ -765,7 +785,7 @@ __device__ __forceinline__ void epi_gather_staged(const T* st, const uint8_t* ss
                                                   int nb, EIn<T>& x) {
   const size_t j = (size_t)b * nx + col, plane = (size_t)nb * nx;
   if (MODE == C_PK_G) { x.c = st[j]; x.p = st[plane + j]; }
-  else if (MODE == C_CG_R) { x.t = st[j]; x.s = ss[j]; }
+  else if (MODE == C_CG_R) { x.t = st[j]; x.g = st[plane + j]; x.s = ss[j]; }
   else if (MODE == C_CG_G) { x.c = st[j]; x.s = ss[j]; }
   else if (MODE == C_GAP) { x.c = st[j]; }
 }
@@ -792,6 +812,9 @@ __device__ __forceinline__ T epi_value(T u, const EIn<T>& x, T* acc) {
   } else if (MODE == C_CG_R) {
     const T rv = x.s ? u : (T)0;
     acc[0] += rv * x.t;
+    acc[1] += rv * x.g;
+    acc[2] += rv * rv;
+    acc[3] += x.g * x.g;
     return rv;
   } else if (MODE == C_CG_G) {
     if (x.s) {
@@ -814,9 +837,9 @@ __device__ __forceinline__ void epi_gather_pair_staged(const T* st, const uint8_
     const V2<T> vc = s2[0], vp = s2[plane / 2];
     x0.c = vc.x; x1.c = vc.y; x0.p = vp.x; x1.p = vp.y;
   } else if (MODE == C_CG_R) {
-    const V2<T> vt = s2[0];
+    const V2<T> vt = s2[0], vg = s2[plane / 2];
     const uchar2 vs = *reinterpret_cast<const uchar2*>(ss + j);
-    x0.t = vt.x; x1.t = vt.y; x0.s = vs.x; x1.s = vs.y;
+    x0.t = vt.x; x1.t = vt.y; x0.g = vg.x; x1.g = vg.y; x0.s = vs.x; x1.s = vs.y;
   } else if (MODE == C_CG_G) {
     const V2<T> vc = s2[0];
     const uchar2 vs = *reinterpret_cast<const uchar2*>(ss + j);
@@ -841,6 +864,9 @@ __device__ __forceinline__ void epi_apply(const PassArgs<T>& a, size_t i, T u, c
     const T rv = x.s ? u : (T)0;
     a.f.r[i] = rv;
     acc[0] += rv * x.t;
+    acc[1] += rv * x.g;
+    acc[2] += rv * rv;
+    acc[3] += x.g * x.g;
   } else if (MODE == C_CG_G) {
     if (x.s) {
       const T gv = u + x.c;
@@ -865,8 +891,8 @@ __device__ __forceinline__ void count_loop(Scalars* sc) {
 // Scalar work of the last CTA of a pass-C launch (FP64): the Polonsky-Keer
 // stopping test and beta after the gap pass, tau after the r pass, tau or the
 // initial residual of the fixed-set CG.
-template <int MODE>
-__device__ __forceinline__ void pass_c_finalize(Scalars* sc, const double (&s2)[2], const double (&s3)[3]) {
+template <typename T, int MODE>
+__device__ __forceinline__ void pass_c_finalize(Scalars* sc, const double (&s2)[4], const double (&s3)[3]) {
   if (MODE == C_PK_G) {
     sc->cnt_c = 0;
     const double G = s2[0], nic = s2[1];
@@ -909,12 +935,52 @@ __device__ __forceinline__ void pass_c_finalize(Scalars* sc, const double (&s2)[
     } else { sc->tau = sgt / srt; sc->have_tau = 1; }
     count_loop(sc);
   } else if (MODE == C_CG_R) {
+    // The residual g here has every update so far applied (pass A applies the
+    // previous iteration's), so |g|^2 = G decides convergence exactly.  Else the
+    // step tau = G / (t . r), and the next residual's norm
+    // |g - tau r|^2 = G - 2 tau g.r + tau^2 |r|^2 from this pass's sums gives
+    // beta = |g - tau r|^2 / G and the stopping test after this update: if it
+    // passes, the solve ends with the update pending (applied by cg_finish),
+    // else the next pass A applies p -= tau t, g -= tau r, t = g + beta t.
+    // The stopping tests compare squares; the scalars this needs are read
+    // before any is written, so their loads overlap.
+    const double stop2 = sc->stop2;
+    const int iter = sc->iter, max_iter = sc->max_iter, loops = sc->loops + 1, max_loops = sc->max_loops;
+    const double str = s2[0], sgr = s2[1], srr = s2[2], G = s2[3];
+    int done = 0, status = SC_OK, have = 0;
+    double tau = 0.0, beta = 0.0, gn = G;
+    if (!isfinite(str) || !isfinite(G) || !isfinite(sgr) || !isfinite(srr)) {
+      status = SC_NUMERIC;
+      done = 1;
+    } else if (G <= stop2 || str <= 0.0) {
+      done = 1;
+    } else if (iter >= max_iter) {
+      status = SC_NOCONV;
+      done = 1;
+    } else {
+      tau = G / str;
+      gn = G - 2.0 * tau * sgr + tau * tau * srr;
+      if (gn < 0.0) gn = 0.0;
+      beta = gn / G;
+      have = 1;
+      if (gn <= stop2) done = 1;  // converged once this update is applied
+    }
+    if (!done && loops >= max_loops) {  // the device-side loop bound (count_loop)
+      status = SC_NOCONV;
+      done = 1;
+    }
+    sc->loops = loops;
     sc->cnt_a = 0;
-    const double str = s2[0];
     sc->str = str;
-    if (!isfinite(str)) { sc->status = SC_NUMERIC; sc->done = 1; }
-    else if (str <= 0.0) { sc->done = 1; }
-    else sc->tau = sc->G / str;
+    sc->G = gn;
+    sc->have_tau = have;
+    if (have) {
+      sc->tau = tau;
+      sc->beta = beta;
+      sc->iter = iter + 1;
+    }
+    if (status != SC_OK) sc->status = status;
+    if (done) sc->done = 1;
   } else if (MODE == C_CG_G) {
     sc->cnt_a = 0;
     const double G = s2[0];
@@ -925,8 +991,9 @@ __device__ __forceinline__ void pass_c_finalize(Scalars* sc, const double (&s2)[
     sc->beta = 0.0;
     sc->iter = 0;
     sc->eps = sqrt(G) / bn;
+    sc->stop2 = (sc->tol * bn) * (sc->tol * bn);  // stop once |g|^2 <= (tol |b|)^2
     if (!isfinite(G)) { sc->status = SC_NUMERIC; sc->done = 1; }
-    else if (sqrt(G) <= sc->tol * bn) sc->done = 1;
+    else if (G <= sc->stop2) sc->done = 1;
   }
 }
 
@@ -936,7 +1003,7 @@ __global__ void BEM_ROW_BOUNDS(LOGL) k_pass_c(PassArgs<T> a) {
   using F = FftC<T, LOGL>;
   constexpr int L = F::L, L8 = F::L8, M = L;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ double red[3 * 32];
+  __shared__ double red[4 * 32];
   __shared__ int lastflag;
   Cx* sm = reinterpret_cast<Cx*>(smem_raw);
   Scalars* sc = a.sc;
@@ -961,7 +1028,7 @@ __global__ void BEM_ROW_BOUNDS(LOGL) k_pass_c(PassArgs<T> a) {
     const int cpr = nx * (int)sizeof(T) / 16;  // 16-byte chunks per row of a T field
 #pragma unroll
     for (int f = 0; f < EpiStage<MODE>::nT; ++f) {
-      const T* src = (MODE == C_PK_G) ? (f == 0 ? a.f.c : a.f.p) : (MODE == C_CG_R ? a.f.t : a.f.c);
+      const T* src = (MODE == C_PK_G) ? (f == 0 ? a.f.c : a.f.p) : (MODE == C_CG_R ? (f == 0 ? a.f.t : a.f.g) : a.f.c);
       for (int q = tid; q < cpr * nb; q += nthr) {
         const int bb = q / cpr, ch = q - bb * cpr;
         cp_async16(reinterpret_cast<char*>(st + ((size_t)f * nb + bb) * nx) + 16 * ch,
@@ -1030,7 +1097,7 @@ __global__ void BEM_ROW_BOUNDS(LOGL) k_pass_c(PassArgs<T> a) {
   // last DIT stage: natural-order outputs z[n] = (x[2n], x[2n+1]) * Px; the
   // epilogue fields are gathered first so their loads overlap the stage
   const T us = (T)a.uscale;
-  T acc[3] = {0, 0, 0};
+  T acc[4] = {0, 0, 0, 0};
   const int row = row0 + b;
   const bool act = row < ny;
   const size_t rowoff = (size_t)row * nx;
@@ -1072,14 +1139,15 @@ __global__ void BEM_ROW_BOUNDS(LOGL) k_pass_c(PassArgs<T> a) {
         epi_apply<T, MODE>(a, rowoff + 2 * n + h, us * (h ? v[e].y : v[e].x), ein[e][h], acc);
   }
   if (MODE == C_PLAIN || MODE == C_GAP) return;
-  block_partials<T, 2>(acc, a.partC + 4 * blockIdx.x, red);
+  constexpr int NQ = MODE == C_CG_R ? 4 : 2;
+  block_partials<T, NQ>(acc, a.partC + 4 * blockIdx.x, red);
   if (!last_block_arrival(MODE == C_PK_G ? &sc->cnt_c : &sc->cnt_a, &lastflag)) return;
-  double s2[2];
-  grid_sum<T, 2>(a.partC, gridDim.x, s2, red);
+  double s2[4] = {0, 0, 0, 0};
+  grid_sum<T, NQ>(a.partC, gridDim.x, s2, red);
   double s3[3] = {0, 0, 0};
   if (MODE == C_PK_G) grid_sum<T, 3>(a.partA, __ldcg(&sc->nA), s3, red);
   if (tid != 0) return;
-  pass_c_finalize<MODE>(sc, s2, s3);
+  pass_c_finalize<T, MODE>(sc, s2, s3);
 }
 
 // ---------------------------------------------------------------------------
@@ -1093,7 +1161,7 @@ __device__ __forceinline__ void pass_cp_body(const PassArgs<T>& a) {
   using F = FftC<T, LOGL>;
   constexpr int L = F::L, L8 = F::L8, M = L;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ double red[3 * 32];
+  __shared__ double red[4 * 32];
   __shared__ int lastflag;
   Cx* sm = reinterpret_cast<Cx*>(smem_raw);
   Scalars* sc = a.sc;
@@ -1166,7 +1234,7 @@ __device__ __forceinline__ void pass_cp_body(const PassArgs<T>& a) {
     mbar_expect_tx(&ebar, (unsigned)rows * (EpiStage<MODE>::nT * rb + (EpiStage<MODE>::S ? (unsigned)nx : 0u)));
 #pragma unroll
     for (int f = 0; f < EpiStage<MODE>::nT; ++f) {
-      const T* src = (MODE == C_PK_G) ? (f == 0 ? a.f.c : a.f.p) : (MODE == C_CG_R ? a.f.t : a.f.c);
+      const T* src = (MODE == C_PK_G) ? (f == 0 ? a.f.c : a.f.p) : (MODE == C_CG_R ? (f == 0 ? a.f.t : a.f.g) : a.f.c);
       for (int bb = 0; bb < rows; ++bb)
         bulk_g2s(st + ((size_t)f * nb + bb) * nx, src + (size_t)(r0 + bb) * nx, rb, &ebar);
     }
@@ -1177,7 +1245,7 @@ __device__ __forceinline__ void pass_cp_body(const PassArgs<T>& a) {
   };
 
   const T us = (T)a.uscale;
-  T acc[3] = {0, 0, 0};
+  T acc[4] = {0, 0, 0, 0};
   const int half = (nx + 1) >> 1;
   // row groups g0 .. gend-1 (fixed-set CG: the contact band only; r = 0 outside it)
   int g0 = 0, gend = G;
@@ -1280,14 +1348,15 @@ __device__ __forceinline__ void pass_cp_body(const PassArgs<T>& a) {
   }
   cp_async_wait_all();
   if (MODE == C_PLAIN || MODE == C_GAP) return;
-  block_partials<T, 2>(acc, a.partC + 4 * blockIdx.x, red);
+  constexpr int NQ = MODE == C_CG_R ? 4 : 2;
+  block_partials<T, NQ>(acc, a.partC + 4 * blockIdx.x, red);
   if (!last_block_arrival(MODE == C_PK_G ? &sc->cnt_c : &sc->cnt_a, &lastflag)) return;
-  double s2[2];
-  grid_sum<T, 2>(a.partC, gridDim.x, s2, red);
+  double s2[4] = {0, 0, 0, 0};
+  grid_sum<T, NQ>(a.partC, gridDim.x, s2, red);
   double s3[3] = {0, 0, 0};
   if (MODE == C_PK_G) grid_sum<T, 3>(a.partA, __ldcg(&sc->nA), s3, red);
   if (tid != 0) return;
-  pass_c_finalize<MODE>(sc, s2, s3);
+  pass_c_finalize<T, MODE>(sc, s2, s3);
 }
 
 template <typename T, int MODE, int LOGL>
@@ -1337,81 +1406,19 @@ __global__ void k_box_scatter(const T* __restrict__ bp, T* __restrict__ p, int n
   }
 }
 
+// The update a fixed-set CG solve ends with when its stopping test passed on
+// the predicted |g - tau r|^2 (pass C leaves it pending): p -= tau t,
+// g -= tau r on the contact band (t and r vanish off the set).
 template <typename T>
-__device__ __forceinline__ T cg_update_one(T* __restrict__ p, T* __restrict__ g, const T* __restrict__ t,
-                                           const T* __restrict__ r, int i, T tau) {
-  const T gv = g[i] - tau * r[i];
-  p[i] -= tau * t[i];
-  g[i] = gv;
-  return gv * gv;
-}
-
-// p -= tau t, g -= tau r on the set (t and r vanish off it); last block forms
-// the new G, beta and the convergence test.  Four elements per thread and
-// trip through vector loads when the pointers allow it.
-template <typename T>
-__device__ __forceinline__ void cg_update_body(int nx, const Fields<T>& f, double* part, Scalars* sc) {
-  __shared__ double red[3 * 32];
-  __shared__ int lastflag;
-  if (sc->done) return;
+__global__ void k_cg_finish(int nx, Fields<T> f, const Scalars* sc) {
+  if (!sc->have_tau) return;
   const T tau = (T)sc->tau;
-  T acc = 0;
-  // only the rows of the contact band: t and r vanish outside it
   const size_t off = (size_t)sc->band0 * nx;
-  const int n = sc->band1 >= sc->band0 ? (sc->band1 - sc->band0 + 1) * nx : 0;
-  T* __restrict__ p = f.p + off;
-  T* __restrict__ g = f.g + off;
-  const T* __restrict__ t = f.t + off;
-  const T* __restrict__ r = f.r + off;
-  if (sizeof(T) == 4 && (nx & 3) == 0) {
-    using V = float4;
-    V* pv = reinterpret_cast<V*>(p);
-    V* gv = reinterpret_cast<V*>(g);
-    const V* tv = reinterpret_cast<const V*>(t);
-    const V* rv = reinterpret_cast<const V*>(r);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (n >> 2); i += gridDim.x * blockDim.x) {
-      V a = pv[i], b = gv[i];
-      const V c = tv[i], d = rv[i];
-      const float tf = (float)tau;
-      a.x -= tf * c.x; a.y -= tf * c.y; a.z -= tf * c.z; a.w -= tf * c.w;
-      b.x -= tf * d.x; b.y -= tf * d.y; b.z -= tf * d.z; b.w -= tf * d.w;
-      pv[i] = a;
-      gv[i] = b;
-      acc += (T)(b.x * b.x + b.y * b.y + b.z * b.z + b.w * b.w);
-    }
-  } else {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-      acc += cg_update_one<T>(p, g, t, r, i, tau);
+  const size_t n = sc->band1 >= sc->band0 ? (size_t)(sc->band1 - sc->band0 + 1) * nx : 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    f.p[off + i] -= tau * f.t[off + i];
+    f.g[off + i] -= tau * f.r[off + i];
   }
-  block_partials<T, 1>(&acc, part + 4 * blockIdx.x, red);
-  if (!last_block_arrival(&sc->cnt_e, &lastflag)) return;
-  double s[1];
-  grid_sum<T, 1>(part, gridDim.x, s, red);
-  if (threadIdx.x != 0) return;
-  sc->cnt_e = 0;
-  const double Gn = s[0];
-  sc->iter += 1;
-  sc->eps = sqrt(Gn) / sc->bnorm;
-  if (!isfinite(Gn)) {
-    sc->status = SC_NUMERIC;
-    sc->done = 1;
-  } else {
-    if (sqrt(Gn) <= sc->tol * sc->bnorm) sc->done = 1;
-    else if (sc->iter >= sc->max_iter) { sc->status = SC_NOCONV; sc->done = 1; }
-    sc->beta = Gn / sc->G;
-    sc->G = Gn;
-  }
-  count_loop(sc);
-}
-
-template <typename T>
-__global__ void k_cg_update(int nx, Fields<T> f, double* part, Scalars* sc) {
-  cg_update_body<T>(nx, f, part, sc);
-}
-template <typename T>
-__global__ void k_cg_update_mi(const PassArgs<T>* __restrict__ arr) {
-  const PassArgs<T>& a = arr[blockIdx.y];
-  cg_update_body<T>(a.pl.nx, a.f, a.partE, a.sc);
 }
 
 // Loop condition of a while-loop graph over several instances: run the body
@@ -1563,7 +1570,8 @@ inline bool aligned16(const void* p) { return p == nullptr || (reinterpret_cast<
 template <typename T, int MODE>
 bool pro_fields_aligned(const PassArgs<T>& a) {
   if (MODE == A_PLAIN) return aligned16(a.f.src);
-  return aligned16(a.f.p) && aligned16(a.f.t) && aligned16(a.f.g) && aligned16(a.f.S);
+  return aligned16(a.f.p) && aligned16(a.f.t) && aligned16(a.f.g) && aligned16(a.f.S) &&
+         (MODE != A_CG_T || aligned16(a.f.r));
 }
 template <typename T>
 bool epi_fields_aligned(const PassArgs<T>& a) {
@@ -1695,10 +1703,6 @@ void launch_pass_c_mi(const PassArgs<T>& a0, int mode, const PassArgs<T>* arr, i
   if (mode == C_PK_G) launch_c_mode_mi<T, C_PK_G>(a0, arr, n, s);
   else if (mode == C_PK_R) launch_c_mode_mi<T, C_PK_R>(a0, arr, n, s);
   else if (mode == C_CG_R) launch_c_mode_mi<T, C_CG_R>(a0, arr, n, s);
-}
-template <typename T>
-void launch_cg_update_mi(const PassArgs<T>* arr, int n, int ngrid, cudaStream_t s) {
-  k_cg_update_mi<T><<<dim3(ngrid, n), 256, 0, s>>>(arr);
 }
 template <typename T>
 void launch_batch_ctl(const PassArgs<T>* arr, int n, unsigned long long cond, cudaStream_t s) {
@@ -1837,8 +1841,8 @@ void launch_box_scatter(const T* bp, T* p, int nx, int ny, int x0, int y0, int b
   k_box_scatter<T><<<ew_grid((size_t)nb), 256, 0, s>>>(bp, p, nx, ny, x0, y0, lbx, nb);
 }
 template <typename T>
-void launch_cg_update(const Plan& pl, Fields<T> f, double* part, Scalars* sc, int ngrid, cudaStream_t s) {
-  k_cg_update<T><<<ngrid, 256, 0, s>>>(pl.nx, f, part, sc);
+void launch_cg_finish(const Plan& pl, Fields<T> f, const Scalars* sc, int ngrid, cudaStream_t s) {
+  k_cg_finish<T><<<ngrid, 256, 0, s>>>(pl.nx, f, sc);
 }
 template <typename T>
 void launch_detach(const Plan& pl, Fields<T> f, double* part, Scalars* sc, int ngrid,
@@ -1891,9 +1895,8 @@ void launch_mask_field(T* x, const uint8_t* S, size_t n, cudaStream_t s) {
   template void launch_box_gather<T>(const T*, const T*, const uint8_t*, int, int, int, int, T*, T*, \
                                      uint8_t*, int, int, cudaStream_t);                         \
   template void launch_box_scatter<T>(const T*, T*, int, int, int, int, int, int, cudaStream_t); \
-  template void launch_cg_update<T>(const Plan&, Fields<T>, double*, Scalars*, int,            \
-                                    cudaStream_t);                                             \
   template void launch_detach<T>(const Plan&, Fields<T>, double*, Scalars*, int, cudaStream_t); \
+  template void launch_cg_finish<T>(const Plan&, Fields<T>, const Scalars*, int, cudaStream_t); \
   template void launch_stats<T>(const Plan&, const T*, const T*, const uint8_t*, int, double*, \
                                 double*, int, cudaStream_t);                                   \
   template void launch_convert_in<T>(const double*, T*, size_t, cudaStream_t);                \
@@ -1901,7 +1904,6 @@ void launch_mask_field(T* x, const uint8_t* S, size_t n, cudaStream_t s) {
   template void launch_offset<T>(const double*, double, T*, size_t, cudaStream_t);            \
   template void launch_set_from_p<T>(const T*, uint8_t*, size_t, cudaStream_t);               \
   template void launch_mask_field<T>(T*, const uint8_t*, size_t, cudaStream_t);                \
-  template void launch_cg_update_mi<T>(const PassArgs<T>*, int, int, cudaStream_t);            \
   template void launch_batch_ctl<T>(const PassArgs<T>*, int, unsigned long long, cudaStream_t);
 
 }  // namespace bem

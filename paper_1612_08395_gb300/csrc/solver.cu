@@ -139,7 +139,7 @@ bool shape_fits(const Plan& pl, int esize) {
   if (pl.threadsA < 64 || pl.threadsA > capA || (pl.threadsA & 31)) return false;
   if (pl.threadsB < 64 || pl.threadsB > capB || (pl.threadsB & 31)) return false;
   const size_t lim = 200 * 1024, rows = (size_t)pl.nbA * pl.nx;
-  if (pl.smemA + (3 * (size_t)esize + 1) * rows + 16 > lim) return false;
+  if (pl.smemA + (4 * (size_t)esize + 1) * rows + 16 > lim) return false;
   if (pass_c_smem(pl.smemC, pl.M, pl.nbA, 2 * esize, (2 * (size_t)esize + 1) * rows) + 32 > lim) return false;
   if (pl.smemB > lim) return false;
   return true;
@@ -373,7 +373,6 @@ PassArgs<T> make_args(bem_ctx* h) {
   a.uscale = h->A / ((double)h->px * (double)h->py);
   a.partA = h->part;
   a.partC = h->partC;
-  a.partE = h->partE;
   a.tmW = h->tmw_ok[sizeof(T) == 8 ? 1 : 0] ? h->tmw[sizeof(T) == 8 ? 1 : 0] : nullptr;
   a.sc = h->sc;
   a.kerr = &h->sc->kerr;
@@ -481,7 +480,6 @@ template <typename T>
 int capture_iterations(bem_ctx* h, bool pk, int iters, cudaEvent_t* ev) {
   PassArgs<T> a = make_args<T>(h);
   a.use_band = pk ? 0 : 1;  // fixed-set CG: only the contact band's rows
-  Fields<T> f = a.f;
   for (int it = 0; it < iters; ++it) {
     const bool mark = ev && it == 0;
     if (mark) cudaEventRecordWithFlags(ev[0], h->stream, cudaEventRecordExternal);
@@ -503,10 +501,8 @@ int capture_iterations(bem_ctx* h, bool pk, int iters, cudaEvent_t* ev) {
       CAPTURE_CHECK("pass B (t)");
       launch_pass_c<T>(a, C_PK_R, h->stream);
       CAPTURE_CHECK("pass C (t)");
-    } else {
-      launch_cg_update<T>(a.pl, f, h->partE, h->sc, h->ew_ngrid, h->stream);
-      CAPTURE_CHECK("cg update");
     }
+    // fixed-set CG: the update of p and g is applied by the next pass A
   }
   return BEM_OK;
 }
@@ -540,7 +536,9 @@ int capture_chunk(bem_ctx* h, bool pk, bool timed, cudaGraphExec_t* out) {
 void add_pass_work(bem_ctx* h, bool pk, int rows, int es) {
   const double nx = h->nx, M = h->px / 2, P = h->py, cx = 2.0 * es;
   const double W = cx * (M + 1) * rows;
-  const double fa = pk ? 4.0 * es : 3.0 * es + 1, fc = pk ? 3.0 * es : 2.0 * es + 1;
+  // fixed-set CG: pass A reads p, g, t, r, S and writes p, g, t; pass C reads
+  // t, g, S and writes r
+  const double fa = pk ? 4.0 * es : 7.0 * es + 1, fc = pk ? 3.0 * es : 3.0 * es + 1;
   h->pass_bytes[0] += fa * nx * rows + W;
   h->pass_bytes[1] += 2 * W + es * (M + 1) * (P / 2 + 1);
   h->pass_bytes[2] += W + fc * nx * rows;
@@ -645,7 +643,7 @@ std::vector<int> loop_key(const LoopReq& r) {
 // The while-loop graph of n instances of one size class: kLoopBody iterations
 // of several-instance passes, then the condition kernel (any instance live).
 template <typename T>
-int capture_loop_mi(LoopBatcher* b, const PassArgs<T>& a0, bool pk, int n, int ew_ngrid, const PassArgs<T>* arr,
+int capture_loop_mi(LoopBatcher* b, const PassArgs<T>& a0, bool pk, int n, const PassArgs<T>* arr,
                     cudaGraphExec_t* out) {
   cudaGraph_t graph = nullptr;
   CK(cudaGraphCreate(&graph, 0));
@@ -677,7 +675,6 @@ int capture_loop_mi(LoopBatcher* b, const PassArgs<T>& a0, bool pk, int n, int e
       launch_pass_a_mi<T>(a0, A_CG_T, arr, n, b->stream);
       launch_pass_b_mi<T>(a0, arr, n, b->stream);
       launch_pass_c_mi<T>(a0, C_CG_R, arr, n, b->stream);
-      launch_cg_update_mi<T>(arr, n, ew_ngrid, b->stream);
     }
   }
   launch_batch_ctl<T>(arr, n, (unsigned long long)cond, b->stream);
@@ -711,7 +708,7 @@ int launch_group(LoopBatcher* b, std::vector<LoopReq*>& g, const std::vector<int
   LoopBatcher::Entry& en = b->graphs[gk];
   if (!en.d_args) CK(cudaMalloc(&en.d_args, sizeof(PassArgs<T>) * (size_t)n));
   if (!en.exec) {
-    CKR(capture_loop_mi<T>(b, host[0], g[0]->pk, n, g[0]->h->ew_ngrid,
+    CKR(capture_loop_mi<T>(b, host[0], g[0]->pk, n,
                            reinterpret_cast<const PassArgs<T>*>(en.d_args), &en.exec));
   }
   // pageable source: the copy is staged before the call returns
@@ -789,7 +786,7 @@ int run_loop_batched(bem_ctx* h, bool pk, int es, bool* solo) {
   if (r.solo) return BEM_OK;
   CKR(read_scalars(h));
   const int ran = h->sc_host->loops - loops0 + 1;
-  h->launches += (unsigned long long)((ran + kLoopBody - 1) / kLoopBody) * kLoopBody * (pk ? 6 : 4);
+  h->launches += (unsigned long long)((ran + kLoopBody - 1) / kLoopBody) * kLoopBody * (pk ? 6 : 3);
   if (!h->sc_host->done) return fail(BEM_ECUDA, "a batched CG loop stopped before the solve was done");
   return BEM_OK;
 }
@@ -813,7 +810,7 @@ int run_loop(bem_ctx* h, cudaGraphExec_t g, cudaGraphExec_t g_timed, int max_ite
   for (int l = 0; l < max_launch; ++l) {
     const bool timed = h->timing && l % kTimeEvery == 0;
     CK(cudaGraphLaunch(timed ? g_timed : g, h->stream));
-    h->launches += (unsigned long long)kChunk * (pk ? 6 : 4);
+    h->launches += (unsigned long long)kChunk * (pk ? 6 : 3);
     CKR(read_scalars(h));
     if (timed) {
       cudaEvent_t* ev = h->ev[pk ? 0 : 1];
@@ -1033,9 +1030,18 @@ int run_fixed_cg(bem_ctx* h, double tol, int max_iter, double pcrit, StepOut* so
   launch_pass_c<T>(a, C_CG_G, h->stream);
   h->launches += 5;
   CKR(read_scalars(h));
-  if (!h->sc_host->done) CKR(run_loop(h, pf.cg_graph[0], pf.cg_graph[1], max_iter, false, (int)sizeof(T)));
+  if (!h->sc_host->done) {
+    CKR(run_loop(h, pf.cg_graph[0], pf.cg_graph[1], max_iter, false, (int)sizeof(T)));
+    if (h->sc_host->have_tau) {
+      Fields<T> f = a.f;
+      launch_cg_finish<T>(a.pl, f, h->sc, h->ew_ngrid, h->stream);
+      h->launches += 1;
+    }
+    so->eps = sqrt(std::max(h->sc_host->G, 0.0)) / h->sc_host->bnorm;
+  } else {
+    so->eps = h->sc_host->eps;
+  }
   so->iterations += h->sc_host->iter;
-  so->eps = h->sc_host->eps;
   if (h->sc_host->status != SC_OK) so->status = map_status(h->sc_host->status);
   if (h->sc_host->status == SC_STALL) so->stalls += 1;
   return BEM_OK;
