@@ -467,23 +467,41 @@ __device__ __forceinline__ void block_partials(const T* acc, double* pp, double*
 }
 
 // Sum of the partials that n CTAs wrote with block_partials<T, NQ>, in a fixed
-// order (deterministic); result in thread 0, as FP64.
+// order (deterministic); result in thread 0, as FP64.  FP32 path: the first
+// warp alone (lane l sums partials l, l + 32, ... with all of a round's loads
+// in flight, then a shuffle tree), so no barrier; every thread must call it
+// in the FP64 path (block reduction).
 template <typename T, int NQ>
 __device__ __forceinline__ void grid_sum(const double* part, int n, double* s, double* red) {
   if constexpr (sizeof(T) == 4) {
+    if (threadIdx.x >= 32) return;
     float2 v[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) v[q] = make_float2(0.f, 0.f);
-    for (int b = threadIdx.x; b < n; b += blockDim.x) {
-      float2 x[NQ];  // all loads in flight before the first use
+    constexpr int R = 4;  // partials per lane and round
+    for (int b0 = (int)threadIdx.x; b0 < n; b0 += 32 * R) {
+      float2 x[R][NQ];
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) x[q] = __ldcg(reinterpret_cast<const float2*>(part + 4 * b + q));
+      for (int r = 0; r < R; ++r) {
+        const int b = b0 + 32 * r;
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) v[q] = ff_add(v[q], x[q]);
+        for (int q = 0; q < NQ; ++q)
+          x[r][q] = b < n ? __ldcg(reinterpret_cast<const float2*>(part + 4 * b + q)) : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) v[q] = ff_add(v[q], x[r][q]);
+      }
     }
-    block_sum_ff<NQ>(v, reinterpret_cast<float2*>(red));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) v[q] = ff_add(v[q], ff_shfl_down(v[q], o));
+    }
 #pragma unroll
     for (int q = 0; q < NQ; ++q) s[q] = ff_to_double(v[q]);
+    (void)red;
   } else {
     double v[NQ];
 #pragma unroll

@@ -891,8 +891,26 @@ __device__ __forceinline__ void count_loop(Scalars* sc) {
 // Scalar work of the last CTA of a pass-C launch (FP64): the Polonsky-Keer
 // stopping test and beta after the gap pass, tau after the r pass, tau or the
 // initial residual of the fixed-set CG.
+// Scalars the fixed-set r pass's last CTA needs, read when every CTA starts
+// (their loads then are off the critical path at the end) by thread 32, so
+// that thread 0 issues the staging copies at once; barriers of the pass order
+// the shared-memory copy before the last CTA's thread 0 reads it.
+struct CgPre {
+  double stop2;
+  int iter, max_iter, loops, max_loops;
+};
+__device__ __forceinline__ void cg_pre_load(const Scalars* sc, CgPre* pre) {
+  if (threadIdx.x != (blockDim.x > 32 ? 32u : 0u)) return;
+  pre->stop2 = sc->stop2;
+  pre->iter = sc->iter;
+  pre->max_iter = sc->max_iter;
+  pre->loops = sc->loops;
+  pre->max_loops = sc->max_loops;
+}
+
 template <typename T, int MODE>
-__device__ __forceinline__ void pass_c_finalize(Scalars* sc, const double (&s2)[4], const double (&s3)[3]) {
+__device__ __forceinline__ void pass_c_finalize(Scalars* sc, const double (&s2)[4], const double (&s3)[3],
+                                                const CgPre& pre) {
   if (MODE == C_PK_G) {
     sc->cnt_c = 0;
     const double G = s2[0], nic = s2[1];
@@ -944,8 +962,8 @@ __device__ __forceinline__ void pass_c_finalize(Scalars* sc, const double (&s2)[
     // else the next pass A applies p -= tau t, g -= tau r, t = g + beta t.
     // The stopping tests compare squares; the scalars this needs are read
     // before any is written, so their loads overlap.
-    const double stop2 = sc->stop2;
-    const int iter = sc->iter, max_iter = sc->max_iter, loops = sc->loops + 1, max_loops = sc->max_loops;
+    const double stop2 = pre.stop2;
+    const int iter = pre.iter, max_iter = pre.max_iter, loops = pre.loops + 1, max_loops = pre.max_loops;
     const double str = s2[0], sgr = s2[1], srr = s2[2], G = s2[3];
     int done = 0, status = SC_OK, have = 0;
     double tau = 0.0, beta = 0.0, gn = G;
@@ -1010,6 +1028,8 @@ __global__ void BEM_ROW_BOUNDS(LOGL) k_pass_c(PassArgs<T> a) {
   if (MODE != C_PLAIN && MODE != C_GAP) {
     if (sc->done) return;
   }
+  __shared__ CgPre pre;
+  if (MODE == C_CG_R) cg_pre_load(sc, &pre);
   const int nb = a.pl.nbA, lognb = a.pl.lognbA, rs = a.pl.gA.rs;
   const int nx = a.pl.nx, ny = a.pl.ny;
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -1147,7 +1167,7 @@ __global__ void BEM_ROW_BOUNDS(LOGL) k_pass_c(PassArgs<T> a) {
   double s3[3] = {0, 0, 0};
   if (MODE == C_PK_G) grid_sum<T, 3>(a.partA, __ldcg(&sc->nA), s3, red);
   if (tid != 0) return;
-  pass_c_finalize<T, MODE>(sc, s2, s3);
+  pass_c_finalize<T, MODE>(sc, s2, s3, pre);
 }
 
 // ---------------------------------------------------------------------------
@@ -1168,6 +1188,8 @@ __device__ __forceinline__ void pass_cp_body(const PassArgs<T>& a) {
   if (MODE != C_PLAIN && MODE != C_GAP) {
     if (sc->done) return;
   }
+  __shared__ CgPre pre;
+  if (MODE == C_CG_R) cg_pre_load(sc, &pre);
   const int nb = a.pl.nbA, lognb = a.pl.lognbA, rs = a.pl.gA.rs;
   const int nx = a.pl.nx, ny = a.pl.ny;
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -1356,7 +1378,7 @@ __device__ __forceinline__ void pass_cp_body(const PassArgs<T>& a) {
   double s3[3] = {0, 0, 0};
   if (MODE == C_PK_G) grid_sum<T, 3>(a.partA, __ldcg(&sc->nA), s3, red);
   if (tid != 0) return;
-  pass_c_finalize<T, MODE>(sc, s2, s3);
+  pass_c_finalize<T, MODE>(sc, s2, s3, pre);
 }
 
 template <typename T, int MODE, int LOGL>
