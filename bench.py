@@ -401,10 +401,12 @@ def kernel_sources_sha():
     return hs.hexdigest()[:16]
 
 
-def profiled_traffic(kernel_key):
+def profiled_traffic(kernel_key, bytes_per_launch):
     """ncu DRAM bytes per launch recorded in profiles/traffic_*.md for this kernel
-    (lines `kernel_key:`, `source_sha16:`, `dram_bytes_per_launch:`), or None if
-    absent or taken on other kernel sources."""
+    (lines `kernel_key:`, `source_sha16:`, `dram_bytes_per_launch:` and, when the
+    captured launch worked on another number of rows than the average timed one,
+    `algorithmic_bytes_of_that_launch:`), scaled to this run's average launch by
+    algorithmic bytes; None if absent or taken on other kernel sources."""
     import glob
     sha = kernel_sources_sha()
     for f in sorted(glob.glob(os.path.join(ROOT, "profiles", "traffic_*.md"))):
@@ -416,9 +418,13 @@ def profiled_traffic(kernel_key):
                     kv[k.strip().lstrip("- ").strip("`")] = v.strip().strip("`")
         if kv.get("kernel_key") == kernel_key and kv.get("source_sha16") == sha:
             try:
-                return float(kv["dram_bytes_per_launch"]), os.path.basename(f)
+                dram = float(kv["dram_bytes_per_launch"])
+                algo = float(kv.get("algorithmic_bytes_of_that_launch", "nan"))
             except (KeyError, ValueError):
                 return None, None
+            if algo > 0 and bytes_per_launch > 0:
+                return dram * bytes_per_launch / algo, os.path.basename(f) + " (scaled by algorithmic bytes)"
+            return dram, os.path.basename(f)
     return None, None
 
 
@@ -579,7 +585,7 @@ def main():
     flops_dom = work_flops[dom]
     achieved = bytes_dom / (avg_ms[dom] * 1e-3) / 1e9
     kernel_key = f"pass {names[dom]}, fixed-set loop, FP32, box torus of the 2048^2 sweep"
-    traffic, traffic_src = profiled_traffic(kernel_key)
+    traffic, traffic_src = profiled_traffic(kernel_key, bytes_dom)
 
     forces = [r.force for r in results]
     counts = [r.contact_count for r in results]
