@@ -591,7 +591,8 @@ def main():
     counts = [r.contact_count for r in results]
     last_contact = max((i for i, c in enumerate(counts) if c > 0), default=0)
     sweep = {"precision": args.precision, "torus": [info.Px, info.Py],
-             "fp32_shapes": {"rows_per_cta": info.rows_per_cta, "cols_per_cta": info.cols_per_cta},
+             "fp32_shapes": {"rows_per_cta": info.rows_per_cta, "cols_per_cta": info.cols_per_cta,
+                             "col_radix": info.col_radix},
              "sweep_s": elapsed / args.steps, "cg_iterations_per_step": iters_total / args.steps,
              "detach_rounds": int(sum(r.detach_rounds for r in results)),
              "stalled_solves": int(sum(r.stalled for r in results)),

@@ -269,6 +269,7 @@ typedef struct {
   unsigned long long kernel_launches; /* kernels launched by this handle so far */
   int rows_per_cta;     /* FP32 row passes: grid rows per CTA            */
   int cols_per_cta;     /* FP32 column pass: columns per CTA             */
+  int col_radix;        /* FP32 column pass: radix of its FFT stages (8 or 16) */
 } bem_info;
 
 int bem_get_info(bem_handle h, bem_info *info);

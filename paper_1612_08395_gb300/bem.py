@@ -64,7 +64,7 @@ class Info(ctypes.Structure):
                 ("nu", ctypes.c_double), ("E0", ctypes.c_double), ("c0", ctypes.c_double),
                 ("alpha", ctypes.c_double), ("compliance", ctypes.c_double),
                 ("device_bytes", ctypes.c_size_t), ("kernel_launches", ctypes.c_ulonglong),
-                ("rows_per_cta", ctypes.c_int), ("cols_per_cta", ctypes.c_int)]
+                ("rows_per_cta", ctypes.c_int), ("cols_per_cta", ctypes.c_int), ("col_radix", ctypes.c_int)]
 
 
 class Job(ctypes.Structure):

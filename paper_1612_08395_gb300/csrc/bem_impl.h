@@ -36,12 +36,17 @@ struct Plan {
   int nbA;    // field rows per CTA in passes A and C (power of two)
   int lognbA;
   int nbB;    // spectrum columns per CTA in pass B
+  int radixB; // pass B (convolution mode): radix-8 stages (Py/8 threads per
+              // column) or radix-16 stages (Py/16 threads, 512 <= Py <= 8192)
   int gridA;  // = ceil(ny / nbA)
   int gridB;  // = ceil((M + 1) / nbB)
   int threadsA, threadsB;
   size_t smemA, smemB, smemC;
   int nsm;    // SMs of the device (persistent launches size their grids by it)
 };
+
+// Largest CTA of the radix-16 column pass for a length-2^LOGL column.
+#define BEM_COL16_MAX_THREADS(LOGL) ((LOGL) >= 13 ? 512 : 256)
 
 // Device-resident scalar state of one CG solve (FP64 throughout).
 struct Scalars {
@@ -113,6 +118,7 @@ struct PassArgs {
   const T* khat;        // B_CONV: spectrum quarter, transposed: [kx][ky], ky <= Py/2
   const void* twA;      // stage twiddle tables, length M (C<T>)
   const void* twB;      // stage twiddle tables, length Py (C<T>)
+  const void* twB16;    // stage twiddle tables of the radix-16 column pass, length Py (C<T>)
   const void* twS;      // exp(-i pi k / M), k = 0..M (C<T>): real-FFT split
   const int* soA;       // index tables of length M and Py (see Geo)
   const int* spA;
@@ -232,6 +238,7 @@ int set_error(int code, const char* msg);
 // of the real-FFT split (M+1 entries), FP64 and FP32 copies.
 void launch_twiddles(double2* t64, float2* t32, int logL, cudaStream_t s);
 void launch_split_twiddles(double2* t64, float2* t32, int M, cudaStream_t s);
+void launch_twiddles16(double2* t64, float2* t32, int logL, cudaStream_t s);
 // Geometry (swizzle, first-stage radix, row stride) of a length-2^logL
 // transform with `rows` transforms per CTA, for elements of esize bytes.
 Geo make_geo(int logL, int rows, int esize);

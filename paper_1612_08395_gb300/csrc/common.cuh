@@ -114,6 +114,64 @@ template <typename T, int S> __device__ __forceinline__ void dft8(C<T>* v) {
   v[3] = add<T>(e3, t3); v[7] = sub<T>(e3, t3);
 }
 
+// 16-point DFT as 4 x 4 (n = n2 + 4 n1, k = k1 + 4 k2): DFT-4 over n1 for
+// each n2, twiddles w16^(S n2 k1), DFT-4 over n2 for each k1; v[0..15] ->
+// X[q] in v[q].  cos(pi/8) and sin(pi/8) are the twiddle w16's components.
+template <typename T, int S> __device__ __forceinline__ void dft16(C<T>* v) {
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) dft4<T, S>(v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]);
+  // v[n2 + 4 k1] = Y[n2][k1]
+  const T c8 = (T)0.92387953251128675613, s8 = (T)0.38268343236508977173, r = consts<T>::rsqrt2;
+  const C<T> w1 = mk<T>(c8, S * s8), w3 = mk<T>(s8, S * c8);
+  v[5] = mul<T>(v[5], w1);    // (1,1): w^1
+  v[15] = mul<T>(v[15], mk<T>(-c8, -S * s8));  // (3,3): w^9 = -w^1
+  v[13] = mul<T>(v[13], w3);  // (1,3): w^3
+  v[7] = mul<T>(v[7], w3);    // (3,1): w^3
+  // (1,2), (2,1): w^2 = (1 + S i)/sqrt2;  (2,3), (3,2): w^6 = (-1 + S i)/sqrt2;  (2,2): w^4 = S i
+  v[9] = mk<T>(r * (v[9].x - S * v[9].y), r * (v[9].y + S * v[9].x));
+  v[6] = mk<T>(r * (v[6].x - S * v[6].y), r * (v[6].y + S * v[6].x));
+  v[14] = mk<T>(r * (-v[14].x - S * v[14].y), r * (-v[14].y + S * v[14].x));
+  v[11] = mk<T>(r * (-v[11].x - S * v[11].y), r * (-v[11].y + S * v[11].x));
+  v[10] = mul_si<T, S>(v[10]);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) dft4<T, S>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+  // v[4 k1 + k2] = X[k1 + 4 k2]: transpose the 4 x 4 index
+  C<T> u[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) u[i] = v[i];
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = u[4 * k1 + k2];
+}
+
+// v[q] *= w^q, q = 1..15; each power formed just before it is used, none more
+// than four products from w.
+template <typename T>
+__device__ __forceinline__ void twiddle16(C<T>* v, C<T> w) {
+  const C<T> w2 = mul<T>(w, w);
+  v[1] = mul<T>(v[1], w);
+  v[2] = mul<T>(v[2], w2);
+  const C<T> w3 = mul<T>(w2, w);
+  v[3] = mul<T>(v[3], w3);
+  const C<T> w4 = mul<T>(w2, w2);
+  v[4] = mul<T>(v[4], w4);
+  const C<T> w5 = mul<T>(w4, w);
+  v[5] = mul<T>(v[5], w5);
+  v[6] = mul<T>(v[6], mul<T>(w3, w3));
+  const C<T> w7 = mul<T>(w4, w3);
+  v[7] = mul<T>(v[7], w7);
+  const C<T> w8 = mul<T>(w4, w4);
+  v[8] = mul<T>(v[8], w8);
+  v[9] = mul<T>(v[9], mul<T>(w8, w));
+  v[10] = mul<T>(v[10], mul<T>(w5, w5));
+  v[11] = mul<T>(v[11], mul<T>(w8, w3));
+  v[12] = mul<T>(v[12], mul<T>(w8, w4));
+  v[13] = mul<T>(v[13], mul<T>(w8, w5));
+  v[14] = mul<T>(v[14], mul<T>(w7, w7));
+  v[15] = mul<T>(v[15], mul<T>(w8, w7));
+}
+
 // ---------------------------------------------------------------------------
 // In-place radix-8 FFT stages in shared memory.
 //

@@ -742,6 +742,219 @@ __global__ void BEM_COL_BOUNDS(LOGL) k_pass_b_mi(const PassArgs<T>* __restrict__
   pass_b_body<T, MODE, LOGL>(arr[blockIdx.y]);
 }
 
+// ---------------------------------------------------------------------------
+// Pass B with radix-16 stages: a length L = 2^LOGL column (512 <= L <= 8192)
+// as a leading stage of radix R0 = 2^(LOGL mod 4) (radix 16 when LOGL is a
+// multiple of 4) with stride 2^LS0 = L/R0, then radix-16 stages with strides
+// 2^(LS0-4), ..., 16, 1.  Thread t (t < L/16) holds the 16 points
+// t + e L/16 in the leading stage (the 16/R0 butterflies t + j L/16), so a
+// forward transform reads only e < 8 (the nonzero half) and the inverse
+// writes only e < 8.  After the stride-1 stage position dig16(k) holds
+// frequency k, and the 16 positions of t's last-stage group hold the
+// frequencies t + q L/16: thread t multiplies those by the spectrum and runs
+// the first inverse stage in registers.  Against the radix-8 pass this takes
+// two fewer shared-memory round trips and barriers per transform (4096
+// points: four barriers instead of six) and a third fewer twiddle stages.
+// The stage table of the leading stage holds exp(-2 pi i o/L), o < 2^LS0;
+// that of the radix-16 stage with stride 2^ls holds exp(-2 pi i o/2^(ls+4)),
+// o < 2^ls; tables concatenated in DIF order.
+template <typename T, int LOGL>
+struct Fft16 {
+  static_assert(LOGL >= 9 && LOGL <= 13, "radix-16 column pass: 512 to 8192 points");
+  static constexpr int L = 1 << LOGL, L16 = L >> 4, RB = LOGL & 3, R0 = RB ? 1 << RB : 16;
+  static constexpr int LS0 = LOGL - (RB ? RB : 4);
+  using G = GeoR16<(int)sizeof(T), LOGL>;
+  static __device__ __forceinline__ int sw(int i) {
+    if (sizeof(T) == 4)
+      return i ^ ((((i >> G::a) ^ (i >> G::b)) & 7) | ((((i >> G::c) ^ (i >> G::d)) & 1) << 3));
+    return i ^ ((((i >> G::a) ^ (i >> G::b)) & 3) | ((((i >> G::c) ^ (i >> G::d)) & 1) << 2));
+  }
+  // position of frequency k (k < L/16) after the DIF stages: digits of k in
+  // the stages' radices, most significant position digit first
+  static __device__ __forceinline__ int dig16(int k) {
+    int p = (k & (R0 - 1)) << LS0;
+    k >>= (RB ? RB : 4);
+#pragma unroll
+    for (int ls = LS0 - 4; ls >= 0; ls -= 4) {
+      p |= (k & 15) << ls;
+      k >>= 4;
+    }
+    return p;
+  }
+  // table offset of the radix-16 stage with stride 2^ls (ls < LS0)
+  static __host__ __device__ constexpr int tw_off(int ls) { return (1 << LS0) + ((1 << LS0) - (1 << (ls + 4))) / 15; }
+
+  static __device__ __forceinline__ void stage0_fwd(C<T>* v, int t, const C<T>* tw) {
+    if constexpr (R0 == 16) {
+      dft16<T, -1>(v);
+      twiddle16<T>(v, __ldg(tw + t));
+    } else {
+      constexpr int J = 16 / R0;
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        C<T> u[R0];
+#pragma unroll
+        for (int r = 0; r < R0; ++r) u[r] = v[j + r * J];
+        const C<T> w = __ldg(tw + t + j * L16);
+        if constexpr (R0 == 8) {
+          dft8<T, -1>(u);
+          twiddle8<T>(u, w);
+        } else if constexpr (R0 == 4) {
+          dft4<T, -1>(u[0], u[1], u[2], u[3]);
+          const C<T> w2 = mul<T>(w, w);
+          u[1] = mul<T>(u[1], w); u[2] = mul<T>(u[2], w2); u[3] = mul<T>(u[3], mul<T>(w2, w));
+        } else {
+          dft2<T, -1>(u[0], u[1]);
+          u[1] = mul<T>(u[1], w);
+        }
+#pragma unroll
+        for (int r = 0; r < R0; ++r) v[j + r * J] = u[r];
+      }
+    }
+  }
+  static __device__ __forceinline__ void stage0_inv(C<T>* v, int t, const C<T>* tw) {
+    if constexpr (R0 == 16) {
+      twiddle16<T>(v, conj<T>(__ldg(tw + t)));
+      dft16<T, 1>(v);
+    } else {
+      constexpr int J = 16 / R0;
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        C<T> u[R0];
+#pragma unroll
+        for (int r = 0; r < R0; ++r) u[r] = v[j + r * J];
+        const C<T> w = conj<T>(__ldg(tw + t + j * L16));
+        if constexpr (R0 == 8) {
+          twiddle8<T>(u, w);
+          dft8<T, 1>(u);
+        } else if constexpr (R0 == 4) {
+          const C<T> w2 = mul<T>(w, w);
+          u[1] = mul<T>(u[1], w); u[2] = mul<T>(u[2], w2); u[3] = mul<T>(u[3], mul<T>(w2, w));
+          dft4<T, 1>(u[0], u[1], u[2], u[3]);
+        } else {
+          u[1] = mul<T>(u[1], w);
+          dft2<T, 1>(u[0], u[1]);
+        }
+#pragma unroll
+        for (int r = 0; r < R0; ++r) v[j + r * J] = u[r];
+      }
+    }
+  }
+  // radix-16 DIF / DIT stage with stride 2^ls, 4 <= ls < LS0 (in shared memory)
+  static __device__ __forceinline__ void dif(C<T>* buf, int t, int ls, const C<T>* tw) {
+    const int o = t & ((1 << ls) - 1);
+    const int sb = sw(((t >> ls) << (ls + 4)) + o);
+    C<T> v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = buf[sb ^ sw(r << ls)];
+    dft16<T, -1>(v);
+    twiddle16<T>(v, __ldg(tw + tw_off(ls) + o));
+#pragma unroll
+    for (int q = 0; q < 16; ++q) buf[sb ^ sw(q << ls)] = v[q];
+  }
+  static __device__ __forceinline__ void dit(C<T>* buf, int t, int ls, const C<T>* tw) {
+    const int o = t & ((1 << ls) - 1);
+    const int sb = sw(((t >> ls) << (ls + 4)) + o);
+    C<T> v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = buf[sb ^ sw(r << ls)];
+    twiddle16<T>(v, conj<T>(__ldg(tw + tw_off(ls) + o)));
+    dft16<T, 1>(v);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) buf[sb ^ sw(q << ls)] = v[q];
+  }
+};
+
+// At most 256 threads per CTA (one 8192-point column: 512) and three CTAs per
+// SM: 80 registers per thread, which leaves a few bytes of spills; at 128
+// registers the pass would run two CTAs per SM.
+#define BEM_COL16_BOUNDS(LOGL) __launch_bounds__(BEM_COL16_MAX_THREADS(LOGL), (LOGL) >= 13 ? 1 : 3)
+template <typename T, int LOGL>
+__device__ __forceinline__ void pass_b16_body(const PassArgs<T>& a) {
+  using Cx = C<T>;
+  using F = Fft16<T, LOGL>;
+  constexpr int L = F::L, L16 = F::L16, hyq = (L >> 1) + 1;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  Cx* sm = reinterpret_cast<Cx*>(smem_raw);
+  if (a.sc != nullptr && a.sc->done) return;
+  const int M = a.pl.M, rin = a.rows_w;
+  const int tid = threadIdx.x;
+  const int c = tid >> (LOGL - 4), t = tid & (L16 - 1);
+  const int kx = blockIdx.x * a.pl.nbB + c;
+  const bool act = kx <= M;
+  Cx* buf = sm + c * L;
+  const Cx* tw = reinterpret_cast<const Cx*>(a.twB16);
+  Cx* W = reinterpret_cast<Cx*>(a.W);
+  const size_t coff = (size_t)(act ? kx : 0) * rin;
+  int ylo = 0, yhi = rin - 1;
+  if (a.use_band) {
+    ylo = a.sc->band0;
+    yhi = min(a.sc->band1, rin - 1);
+  }
+
+  Cx v[16];
+#pragma unroll
+  for (int e = 0; e < 16; ++e) {
+    v[e] = mk<T>(0, 0);
+    if (e >= 8) continue;
+    const int y = t + e * L16;
+    if (act && y >= ylo && y <= yhi && bem_check(coff + y < (size_t)(M + 1) * rin, a.kerr)) v[e] = W[coff + y];
+  }
+  F::stage0_fwd(v, t, tw);
+#pragma unroll
+  for (int e = 0; e < 16; ++e) buf[F::sw(t + e * L16)] = v[e];
+  __syncthreads();
+#pragma unroll
+  for (int ls = F::LS0 - 4; ls >= 4; ls -= 4) {
+    F::dif(buf, t, ls, tw);
+    __syncthreads();
+  }
+  // stride-1 stage, spectrum multiply and the first inverse stage in registers
+  {
+    const int gb = F::sw(F::dig16(t));
+    const T* kc = a.khat + (size_t)(act ? kx : 0) * hyq;
+    T kf[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int ky = t + q * L16;
+      const int kk = ky <= (L >> 1) ? ky : L - ky;
+      kf[q] = act ? __ldg(kc + kk) : (T)0;
+    }
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = buf[gb ^ F::sw(r)];
+    dft16<T, -1>(v);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = scale<T>(v[q], kf[q]);
+    dft16<T, 1>(v);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) buf[gb ^ F::sw(r)] = v[r];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int ls = 4; ls <= F::LS0 - 4; ls += 4) {
+    F::dit(buf, t, ls, tw);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int e = 0; e < 16; ++e) v[e] = buf[F::sw(t + e * L16)];
+  F::stage0_inv(v, t, tw);
+  if (act) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int y = t + e * L16;
+      if (y >= ylo && y <= yhi && bem_check(coff + y < (size_t)(M + 1) * rin, a.kerr)) W[coff + y] = v[e];
+    }
+  }
+}
+template <typename T, int LOGL>
+__global__ void BEM_COL16_BOUNDS(LOGL) k_pass_b16(PassArgs<T> a) {
+  pass_b16_body<T, LOGL>(a);
+}
+template <typename T, int LOGL>
+__global__ void BEM_COL16_BOUNDS(LOGL) k_pass_b16_mi(const PassArgs<T>* __restrict__ arr) {
+  pass_b16_body<T, LOGL>(arr[blockIdx.y]);
+}
+
 // Epilogue fields of pass C that are prefetched into shared memory at kernel
 // start (their loads then overlap the inverse transform): number of T-typed
 // fields and whether the contact set S (one byte per element) is staged.
@@ -1626,9 +1839,18 @@ void launch_a_mode(const PassArgs<T>& a, cudaStream_t s) {
 #undef BEM_CASE
   }
 }
+#define BEM_LOGL_CASES_B16(X) X(9) X(10) X(11) X(12) X(13)
 template <typename T, int MODE>
 void launch_b_mode(const PassArgs<T>& a, cudaStream_t s) {
   const dim3 grid(a.pl.gridB), block(a.pl.threadsB);
+  if (MODE == B_CONV && a.pl.radixB == 16) {
+    switch (a.pl.gB.logL) {
+#define BEM_CASE(LG) case LG: k_pass_b16<T, LG><<<grid, block, a.pl.smemB, s>>>(a); break;
+      BEM_LOGL_CASES_B16(BEM_CASE)
+#undef BEM_CASE
+    }
+    return;
+  }
   switch (a.pl.gB.logL) {
 #define BEM_CASE(LG) case LG: k_pass_b<T, MODE, LG><<<grid, block, a.pl.smemB, s>>>(a); break;
     BEM_LOGL_CASES_B(BEM_CASE)
@@ -1714,6 +1936,14 @@ void launch_pass_b_mi(const PassArgs<T>& a0, const PassArgs<T>* arr, int n, cuda
     }
   }
   const dim3 grid(a0.pl.gridB, n), block(a0.pl.threadsB);
+  if (a0.pl.radixB == 16) {
+    switch (a0.pl.gB.logL) {
+#define BEM_CASE(LG) case LG: k_pass_b16_mi<T, LG><<<grid, block, a0.pl.smemB, s>>>(arr); break;
+      BEM_LOGL_CASES_B16(BEM_CASE)
+#undef BEM_CASE
+    }
+    return;
+  }
   switch (a0.pl.gB.logL) {
 #define BEM_CASE(LG) case LG: k_pass_b_mi<T, B_CONV, LG><<<grid, block, a0.pl.smemB, s>>>(arr); break;
     BEM_LOGL_CASES_B(BEM_CASE)
@@ -1808,6 +2038,9 @@ cudaError_t set_smem_attrs_b(int bytes) {
 #define BEM_CASE(LG) \
   BEM_ATTR((k_pass_b<T, B_CONV, LG>)) BEM_ATTR((k_pass_b<T, B_SPECTRUM, LG>)) BEM_ATTR((k_pass_b_mi<T, B_CONV, LG>))
   BEM_LOGL_CASES_B(BEM_CASE)
+#undef BEM_CASE
+#define BEM_CASE(LG) BEM_ATTR((k_pass_b16<T, LG>)) BEM_ATTR((k_pass_b16_mi<T, LG>))
+  BEM_LOGL_CASES_B16(BEM_CASE)
 #undef BEM_CASE
   return e;
 }

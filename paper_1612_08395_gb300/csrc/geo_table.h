@@ -47,4 +47,24 @@ struct GeoC {
   static constexpr int d = (ESIZE == 4 ? kGeo8 : kGeo16)[LOGL - 3].d;
 };
 
+// Swizzles {a, b, c, d} of the radix-16 column transform (lengths 2^9 .. 2^13,
+// one column per 2^(LOGL-4) threads, no row pad), same form as above, found by
+// exhaustive search for conflict-free stage-0, middle-stage and last-stage
+// (digit-reversed group) accesses: 8-byte elements by half-warps, 16-byte
+// elements by quarter-warps.
+struct GeoR16Row {
+  int a, b, c, d;
+};
+constexpr GeoR16Row kGeoR16_8[5] = {
+  {4, 5, 4, 8}, {4, 6, 4, 9}, {4, 7, 4, 10}, {4, 8, 4, 11}, {4, 8, 4, 12}};
+constexpr GeoR16Row kGeoR16_16[5] = {
+  {3, 4, 3, 8}, {3, 8, 3, 4}, {3, 8, 3, 10}, {3, 8, 3, 10}, {3, 8, 3, 12}};
+template <int ESIZE, int LOGL>
+struct GeoR16 {
+  static constexpr int a = (ESIZE == 4 ? kGeoR16_8 : kGeoR16_16)[LOGL - 9].a;
+  static constexpr int b = (ESIZE == 4 ? kGeoR16_8 : kGeoR16_16)[LOGL - 9].b;
+  static constexpr int c = (ESIZE == 4 ? kGeoR16_8 : kGeoR16_16)[LOGL - 9].c;
+  static constexpr int d = (ESIZE == 4 ? kGeoR16_8 : kGeoR16_16)[LOGL - 9].d;
+};
+
 }  // namespace bem

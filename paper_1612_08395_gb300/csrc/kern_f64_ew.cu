@@ -63,6 +63,33 @@ void launch_twiddles(double2* t64, float2* t32, int logL, cudaStream_t s) {
   k_twiddles<<<64, 256, 0, s>>>(t64, t32, logL);
 }
 
+// Stage twiddle tables of the radix-16 column pass of length 2^logL (9 <= logL
+// <= 13; other lengths have no such pass and get no table): a leading stage
+// of radix R0 = 2^(logL mod 4) (16 if that is 1) and stride s = 2^logL/R0,
+// then radix-16 stages; the table of stage (R, s) holds exp(-2 pi i o/(R s))
+// for o < s, tables concatenated in DIF order.  Computed in FP64.
+__global__ void k_twiddles16(double2* t64, float2* t32, int logL) {
+  if (logL < 9 || logL > 13) return;
+  const int rb = logL & 3;
+  int R = rb ? 1 << rb : 16;
+  int s = (1 << logL) / R;
+  int off = 0;
+  while (s > 1) {
+    for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < s; o += gridDim.x * blockDim.x) {
+      double sn, cs;
+      sincospi(-2.0 * (double)o / ((double)R * (double)s), &sn, &cs);
+      t64[off + o] = make_double2(cs, sn);
+      t32[off + o] = make_float2((float)cs, (float)sn);
+    }
+    off += s;
+    R = 16;
+    s /= 16;
+  }
+}
+void launch_twiddles16(double2* t64, float2* t32, int logL, cudaStream_t s) {
+  k_twiddles16<<<64, 256, 0, s>>>(t64, t32, logL);
+}
+
 // exp(-i pi k / M), k = 0..M: the real-FFT split of a length-2M real transform.
 __global__ void k_split_twiddles(double2* t64, float2* t32, int M) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= M; k += gridDim.x * blockDim.x) {

@@ -107,9 +107,9 @@ int pow2_at_least(int v) { int p = 1; while (p < v) p <<= 1; return p; }
 constexpr int kMinThreads = 64;
 constexpr int kCtasPerSm = 2;
 
-// The plan for given rows per CTA of the row passes (nbA) and columns per CTA
-// of the column pass (nbB).
-Plan plan_with(int nx, int ny, int px, int py, int esize, int nsm, int nbA, int nbB) {
+// The plan for given rows per CTA of the row passes (nbA), columns per CTA of
+// the column pass (nbB) and radix of the column pass's stages (8 or 16).
+Plan plan_with(int nx, int ny, int px, int py, int esize, int nsm, int nbA, int nbB, int radixB = 8) {
   Plan pl{};
   pl.nx = nx; pl.ny = ny; pl.px = px; pl.py = py;
   pl.M = px / 2;
@@ -122,10 +122,12 @@ Plan plan_with(int nx, int ny, int px, int py, int esize, int nsm, int nbA, int 
   pl.smemA = (size_t)nbA * pl.gA.rs * 2 * esize;
   pl.smemC = pl.smemA;
   pl.nbB = nbB;
+  pl.radixB = radixB;
   pl.gB = make_geo(logPy, nbB, esize);
-  pl.threadsB = nbB * (py / 8);
+  pl.threadsB = nbB * (py / radixB);
   pl.gridB = (pl.M + 1 + nbB - 1) / nbB;
-  pl.smemB = (size_t)nbB * pl.gB.rs * 2 * esize;
+  // the radix-16 pass needs no row pad (its swizzle spreads every access)
+  pl.smemB = (size_t)nbB * (radixB == 16 ? py : pl.gB.rs) * 2 * esize;
   pl.nsm = nsm;
   return pl;
 }
@@ -134,15 +136,43 @@ Plan plan_with(int nx, int ny, int px, int py, int esize, int nsm, int nbA, int 
 // bounds, and shared memory (with the persistent passes' staging) in budget.
 bool shape_fits(const Plan& pl, int esize) {
   const int logM = ilog2(pl.M), logPy = ilog2(pl.py);
-  const int capA = logM >= 13 ? 1024 : 512, capB = logPy >= 13 ? 1024 : 512;
+  const int capA = logM >= 13 ? 1024 : 512;
+  const int capB = pl.radixB == 16 ? BEM_COL16_MAX_THREADS(logPy) : logPy >= 13 ? 1024 : 512;
   if (pl.nbA < 1 || pl.nbA > 64 || pl.nbB < 1 || pl.nbB > 64) return false;
   if (pl.threadsA < 64 || pl.threadsA > capA || (pl.threadsA & 31)) return false;
   if (pl.threadsB < 64 || pl.threadsB > capB || (pl.threadsB & 31)) return false;
+  // radix-16 column pass: FP32, 512 to 8192 points (whole warps per column)
+  if (pl.radixB != 8 && (pl.radixB != 16 || esize != 4 || logPy < 9 || logPy > 13)) return false;
   const size_t lim = 200 * 1024, rows = (size_t)pl.nbA * pl.nx;
   if (pl.smemA + (4 * (size_t)esize + 1) * rows + 16 > lim) return false;
   if (pass_c_smem(pl.smemC, pl.M, pl.nbA, 2 * esize, (2 * (size_t)esize + 1) * rows) + 32 > lim) return false;
   if (pl.smemB > lim) return false;
   return true;
+}
+
+// Columns per CTA of the column pass: about 256 threads per CTA, and for small
+// grids about two CTAs per SM.
+int default_cols_b(int M, int py, int esize, int nsm, int radix) {
+  const int tb = py / radix;
+  int nbb = 256 / tb;
+  if (nbb < 1) nbb = 1;
+  while (nbb > 1 && (size_t)nbb * (py + 32) * 2 * esize > 128 * 1024) nbb >>= 1;
+  while (nbb > 1 && (nbb / 2) * tb >= kMinThreads && (M + nbb) / nbb < kCtasPerSm * nsm) nbb >>= 1;
+  return nbb;
+}
+
+// Radix of the column pass before tuning: radix-8 stages, or the radix-16
+// pass where BEM_RADIX_B=16 asks for it and it applies (FP32, 512 to 8192
+// points); the FP32 autotuner chooses between them per grid size.
+int forced_radix_b() {
+  const char* env = getenv("BEM_RADIX_B");
+  const int r = env ? atoi(env) : 0;
+  return r == 8 || r == 16 ? r : 0;
+}
+int default_radix_b(int py, int esize) {
+  const int logPy = ilog2(py);
+  if (forced_radix_b() == 16 && esize == 4 && logPy >= 9 && logPy <= 13) return 16;
+  return 8;
 }
 
 // Default shapes: about 256 threads per CTA, rows of W written in 32-byte
@@ -157,12 +187,8 @@ Plan make_plan(int nx, int ny, int px, int py, int esize, int nsm) {
   while (nb > 1 && nb * tr > BEM_MAX_THREADS_A) nb >>= 1;
   while (nb > 1 && (size_t)nb * (M + 32) * 2 * esize > 128 * 1024) nb >>= 1;
   while (nb > 1 && (nb / 2) * tr >= kMinThreads && (ny + nb - 1) / nb < kCtasPerSm * nsm) nb >>= 1;
-  const int tb = py / 8;
-  int nbb = 256 / tb;
-  if (nbb < 1) nbb = 1;
-  while (nbb > 1 && (size_t)nbb * (py + 32) * 2 * esize > 128 * 1024) nbb >>= 1;
-  while (nbb > 1 && (nbb / 2) * tb >= kMinThreads && (M + nbb) / nbb < kCtasPerSm * nsm) nbb >>= 1;
-  return plan_with(nx, ny, px, py, esize, nsm, nb, nbb);
+  const int radix = default_radix_b(py, esize);
+  return plan_with(nx, ny, px, py, esize, nsm, nb, default_cols_b(M, py, esize, nsm, radix), radix);
 }
 
 }  // namespace
@@ -361,9 +387,9 @@ PassArgs<T> make_args(bem_ctx* h) {
   a.khat = khat_of<T>(h);
   const size_t M = h->px / 2, P = h->py;
   if constexpr (sizeof(T) == 8) {
-    a.twA = h->tw64; a.twB = h->tw64 + M; a.twS = h->tw64 + M + P;
+    a.twA = h->tw64; a.twB = h->tw64 + M; a.twS = h->tw64 + M + P; a.twB16 = h->tw64 + M + P + M + 1;
   } else {
-    a.twA = h->tw32; a.twB = h->tw32 + M; a.twS = h->tw32 + M + P;
+    a.twA = h->tw32; a.twB = h->tw32 + M; a.twS = h->tw32 + M + P; a.twB16 = h->tw32 + M + P + M + 1;
   }
   const int* gt = h->geo + (sizeof(T) == 8 ? 2 * kSoEntries + M + P : 0);
   a.soA = gt;
@@ -637,7 +663,7 @@ namespace {
 // shape, so one several-instance launch per pass serves them all.
 std::vector<int> loop_key(const LoopReq& r) {
   const Plan& pl = r.es == 4 ? r.a32.pl : r.a64.pl;
-  return {r.es, r.pk ? 1 : 0, pl.nx, pl.ny, pl.px, pl.py, pl.nbA, pl.nbB, r.h->ew_ngrid};
+  return {r.es, r.pk ? 1 : 0, pl.nx, pl.ny, pl.px, pl.py, pl.nbA, pl.nbB, pl.radixB, r.h->ew_ngrid};
 }
 
 // The while-loop graph of n instances of one size class: kLoopBody iterations
@@ -1175,13 +1201,17 @@ int refine(bem_ctx* h, double d, bool adhesive, int sweeps, double tol64, double
 // noise keeps the default).  The choice is kept for the process, and the lock
 // is held while timing, so every context of a size uses the same shapes.
 struct ShapeKey {
-  int nx, ny, px, py;
+  int nx, ny, px, py, radix_req;  // radix_req: the column-pass radix BEM_RADIX_B fixes (0: none)
   bool operator<(const ShapeKey& o) const {
-    return nx != o.nx ? nx < o.nx : ny != o.ny ? ny < o.ny : px != o.px ? px < o.px : py < o.py;
+    return nx != o.nx ? nx < o.nx : ny != o.ny ? ny < o.ny : px != o.px ? px < o.px : py != o.py ? py < o.py
+                                                                                      : radix_req < o.radix_req;
   }
 };
 std::mutex g_tune_mu;
-std::map<ShapeKey, std::pair<int, int>> g_tuned;
+struct Tuned {
+  int nbA, nbB, radixB;
+};
+std::map<ShapeKey, Tuned> g_tuned;
 
 int set_plan32(bem_ctx* h, const Plan& pl) {
   h->plan32 = pl;
@@ -1229,48 +1259,66 @@ int autotune32(bem_ctx* h) {
   const char* env = getenv("BEM_AUTOTUNE");
   if (env && env[0] == '0') return BEM_OK;
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  const ShapeKey key{h->nx, h->ny, h->px, h->py};
+  const ShapeKey key{h->nx, h->ny, h->px, h->py, forced_radix_b()};
   const Plan base = h->plan32;
   auto it = g_tuned.find(key);
   if (it != g_tuned.end()) {
-    if (it->second.first != base.nbA || it->second.second != base.nbB)
-      CKR(set_plan32(h, plan_with(h->nx, h->ny, h->px, h->py, 4, base.nsm, it->second.first, it->second.second)));
+    const Tuned& u = it->second;
+    if (u.nbA != base.nbA || u.nbB != base.nbB || u.radixB != base.radixB)
+      CKR(set_plan32(h, plan_with(h->nx, h->ny, h->px, h->py, 4, base.nsm, u.nbA, u.nbB, u.radixB)));
     return BEM_OK;
   }
   CKR(ensure_fields<float>(h));
   // Candidates: the default shapes, half and twice the rows per CTA of the row
-  // passes, half and twice the columns per CTA of the column pass.  Each is
+  // passes, half and twice the columns per CTA of the column pass, and the
+  // column pass in the other radix (8 or 16) at its default columns per CTA
+  // and half and twice that (unless BEM_RADIX_B fixes the radix).  Each is
   // timed in three interleaved rounds and keeps its fastest round, so that a
   // slow round (clock ramp, another process) cannot pick a shape.
-  struct Cand { int nbA, nbB; double t[3]; };
+  struct Cand { int nbA, nbB, radixB; double t[3]; };
   std::vector<Cand> cand;
-  cand.push_back({base.nbA, base.nbB, {1e30, 1e30, 1e30}});
+  auto fits = [&](int nbA, int nbB, int radixB) {
+    return nbA >= 1 && nbB >= 1 &&
+           shape_fits(plan_with(h->nx, h->ny, h->px, h->py, 4, base.nsm, nbA, nbB, radixB), 4);
+  };
+  cand.push_back({base.nbA, base.nbB, base.radixB, {1e30, 1e30, 1e30}});
   for (int nb : {base.nbA / 2, base.nbA * 2})
-    if (nb >= 1 && shape_fits(plan_with(h->nx, h->ny, h->px, h->py, 4, base.nsm, nb, base.nbB), 4))
-      cand.push_back({nb, base.nbB, {1e30, 1e30, 1e30}});
+    if (fits(nb, base.nbB, base.radixB)) cand.push_back({nb, base.nbB, base.radixB, {1e30, 1e30, 1e30}});
   for (int nb : {base.nbB / 2, base.nbB * 2})
-    if (nb >= 1 && shape_fits(plan_with(h->nx, h->ny, h->px, h->py, 4, base.nsm, base.nbA, nb), 4))
-      cand.push_back({base.nbA, nb, {1e30, 1e30, 1e30}});
+    if (fits(base.nbA, nb, base.radixB)) cand.push_back({base.nbA, nb, base.radixB, {1e30, 1e30, 1e30}});
+  if (!forced_radix_b()) {
+    const int other = base.radixB == 8 ? 16 : 8;
+    const int nbo = default_cols_b(h->px / 2, h->py, 4, base.nsm, other);
+    for (int nb : {nbo, nbo / 2, nbo * 2})
+      if (fits(base.nbA, nb, other)) cand.push_back({base.nbA, nb, other, {1e30, 1e30, 1e30}});
+  }
   constexpr int reps = 6, rounds = 3;
   for (int r = 0; r < rounds; ++r) {
     for (Cand& c : cand) {
-      CKR(set_plan32(h, plan_with(h->nx, h->ny, h->px, h->py, 4, base.nsm, c.nbA, c.nbB)));
+      CKR(set_plan32(h, plan_with(h->nx, h->ny, h->px, h->py, 4, base.nsm, c.nbA, c.nbB, c.radixB)));
       double t[3];
       CKR(time_passes32(h, reps, t));
       for (int q = 0; q < 3; ++q) c.t[q] = std::min(c.t[q], t[q]);
     }
   }
   // a change needs a 3% gain over the default shapes
-  int bestA = base.nbA, bestB = base.nbB;
+  int bestA = base.nbA, bestB = base.nbB, bestR = base.radixB;
   double tAC = cand[0].t[0] + cand[0].t[2], tB = cand[0].t[1];
   for (size_t c = 1; c < cand.size(); ++c) {
     const Cand& x = cand[c];
-    if (x.nbB == base.nbB && x.t[0] + x.t[2] < 0.97 * tAC) { tAC = x.t[0] + x.t[2]; bestA = x.nbA; }
-    if (x.nbA == base.nbA && x.t[1] < 0.97 * tB) { tB = x.t[1]; bestB = x.nbB; }
+    if (x.nbB == base.nbB && x.radixB == base.radixB && x.t[0] + x.t[2] < 0.97 * tAC) {
+      tAC = x.t[0] + x.t[2];
+      bestA = x.nbA;
+    }
+    if (x.nbA == base.nbA && x.t[1] < 0.97 * tB) {
+      tB = x.t[1];
+      bestB = x.nbB;
+      bestR = x.radixB;
+    }
   }
-  CKR(set_plan32(h, plan_with(h->nx, h->ny, h->px, h->py, 4, base.nsm, bestA, bestB)));
+  CKR(set_plan32(h, plan_with(h->nx, h->ny, h->px, h->py, 4, base.nsm, bestA, bestB, bestR)));
   CK(cudaStreamSynchronize(h->stream));
-  g_tuned[key] = {bestA, bestB};
+  g_tuned[key] = {bestA, bestB, bestR};
   return BEM_OK;
 }
 
@@ -1342,7 +1390,8 @@ static int create_ctx(int Nx, int Ny, double dx, double dy, double k, double nu,
   const size_t n = (size_t)Nx * Ny;
   int rc;
   if ((rc = dmalloc(h, (void**)&h->kq64, sizeof(double) * (size_t)hyq * (M + 1)))) return cleanup(rc);
-  const size_t ntw = (size_t)M + h->py + M + 1;
+  // [length-M stages | length-Py stages | split | radix-16 length-Py stages]
+  const size_t ntw = (size_t)M + h->py + M + 1 + h->py;
   if ((rc = dmalloc(h, (void**)&h->tw64, sizeof(double2) * ntw))) return cleanup(rc);
   if ((rc = dmalloc(h, (void**)&h->tw32, sizeof(float2) * ntw))) return cleanup(rc);
   if ((rc = dmalloc(h, (void**)&h->geo, sizeof(int) * 2 * (2 * kSoEntries + M + h->py)))) return cleanup(rc);
@@ -1383,6 +1432,7 @@ static int create_ctx(int Nx, int Ny, double dx, double dy, double k, double nu,
   launch_twiddles(h->tw64, h->tw32, ilog2(M), h->stream);
   launch_twiddles(h->tw64 + M, h->tw32 + M, ilog2(h->py), h->stream);
   launch_split_twiddles(h->tw64 + M + h->py, h->tw32 + M + h->py, M, h->stream);
+  launch_twiddles16(h->tw64 + M + h->py + M + 1, h->tw32 + M + h->py + M + 1, ilog2(h->py), h->stream);
   // a1: influence coefficients on the offsets 0..Px/2, 0..Py/2 (Eq. 9)
   if (parent) {
     const size_t pw = (size_t)parent->px / 2 + 1;
@@ -1455,6 +1505,7 @@ extern "C" int bem_get_info(bem_handle h, bem_info* info) {
   info->alpha = h->alpha; info->compliance = h->A; info->device_bytes = h->bytes;
   info->rows_per_cta = h->plan32.nbA;
   info->cols_per_cta = h->plan32.nbB;
+  info->col_radix = h->plan32.radixB;
   for (const bem_ctx* c : h->subs) info->device_bytes += c->bytes;
   info->kernel_launches = h->launches;
   return BEM_OK;

@@ -1,7 +1,8 @@
 """Launch-shape autotuner of the FP32 passes: every handle of a grid size in a
-process gets the shapes the first one chose, the shapes are launchable, and a
-solve with tuned shapes agrees with one at the default shapes (a process with
-BEM_AUTOTUNE=0) within the FP32 path's tolerance."""
+process gets the shapes the first one chose, the shapes are launchable (the
+radix-16 column pass only where it exists), and a solve with tuned shapes
+agrees with one at the default shapes (a process with BEM_AUTOTUNE=0) within
+the FP32 path's tolerance."""
 import json
 import os
 import subprocess
@@ -37,9 +38,12 @@ def test_same_size_same_shapes(bem_mod, cuda_ok):
         with bem_mod.Handle(n, n, 1.0 / n, 1.0 / n, 0.3, 0.3) as a, \
                 bem_mod.Handle(n, n, 1.0 / n, 1.0 / n, -0.4, 0.2) as b:
             ia, ib = a.info(), b.info()
-        assert (ia.rows_per_cta, ia.cols_per_cta) == (ib.rows_per_cta, ib.cols_per_cta)
+        assert (ia.rows_per_cta, ia.cols_per_cta, ia.col_radix) == (ib.rows_per_cta, ib.cols_per_cta,
+                                                                    ib.col_radix)
         for v in (ia.rows_per_cta, ia.cols_per_cta):
             assert v >= 1 and v & (v - 1) == 0
+        # the radix-16 column pass exists for 512- to 8192-point columns only
+        assert ia.col_radix in ((8, 16) if n >= 256 else (8,))
 
 
 @pytest.mark.parametrize("n", [256, 1024])
