@@ -241,6 +241,19 @@ __device__ __forceinline__ void twiddle8(C<T>* v, C<T> w) {
   v[7] = mul<T>(v[7], mul<T>(w4, w3));
 }
 
+// v[q] *= pw[(q-1) s] (or its conjugate), q = 1..7: the powers read from a
+// table instead of formed by multiplication.  The FP64 path uses this: at
+// GB300's FP64 rate the six products that form the powers cost more than the
+// seven coalesced table loads.
+template <typename T, bool CONJ>
+__device__ __forceinline__ void twiddle8_pow(C<T>* v, const C<T>* pw, int s) {
+#pragma unroll
+  for (int q = 1; q < 8; ++q) {
+    const C<T> w = __ldg(pw + (q - 1) * s);
+    v[q] = mul<T>(v[q], CONJ ? conj<T>(w) : w);
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void powers8(C<T> w, C<T>* wp) {
   wp[1] = w;

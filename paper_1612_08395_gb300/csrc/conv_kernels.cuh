@@ -63,18 +63,30 @@ struct FftC {
   static __device__ __forceinline__ constexpr bool first_half(int e) {
     return R0 == 0 ? e < 4 : (R0 == 2 ? (e & 3) < 2 : (e & 1) == 0);
   }
+  // FP64 tables hold every power a butterfly needs (see twiddle8_pow): offset
+  // of the radix-8 stage with stride 2^ls there
+  static __device__ __forceinline__ constexpr int pow_off(int ls) {
+    return (R0 ? ((1 << R0) - 1) << (LOGL - R0) : 0) + (1 << (LOGL - R0)) - (8 << ls);
+  }
   // stage 0 butterflies on the 8 values of a thread (DIF: butterfly, then twiddle)
   static __device__ __forceinline__ void stage0_fwd(C<T>* v, int t, const C<T>* tw) {
     if (R0 == 0) {
       dft8<T, -1>(v);
-      twiddle8<T>(v, __ldg(tw + t));
+      if constexpr (sizeof(T) == 8) twiddle8_pow<T, false>(v, tw + t, L8);
+      else twiddle8<T>(v, __ldg(tw + t));
     } else if (R0 == 2) {
 #pragma unroll
       for (int i = 0; i < 2; ++i) {
         C<T>* u = v + 4 * i;
         dft4<T, -1>(u[0], u[1], u[2], u[3]);
-        const C<T> w = __ldg(tw + t + i * L8), w2 = mul<T>(w, w), w3 = mul<T>(w2, w);
-        u[1] = mul<T>(u[1], w); u[2] = mul<T>(u[2], w2); u[3] = mul<T>(u[3], w3);
+        if constexpr (sizeof(T) == 8) {
+          const C<T>* pw = tw + t + i * L8;
+          u[1] = mul<T>(u[1], __ldg(pw)); u[2] = mul<T>(u[2], __ldg(pw + (L >> 2)));
+          u[3] = mul<T>(u[3], __ldg(pw + 2 * (L >> 2)));
+        } else {
+          const C<T> w = __ldg(tw + t + i * L8), w2 = mul<T>(w, w), w3 = mul<T>(w2, w);
+          u[1] = mul<T>(u[1], w); u[2] = mul<T>(u[2], w2); u[3] = mul<T>(u[3], w3);
+        }
       }
     } else {
 #pragma unroll
@@ -88,14 +100,21 @@ struct FftC {
   // inverse of stage 0 (DIT: conjugate twiddle, then butterfly)
   static __device__ __forceinline__ void stage0_inv(C<T>* v, int t, const C<T>* tw) {
     if (R0 == 0) {
-      twiddle8<T>(v, conj<T>(__ldg(tw + t)));
+      if constexpr (sizeof(T) == 8) twiddle8_pow<T, true>(v, tw + t, L8);
+      else twiddle8<T>(v, conj<T>(__ldg(tw + t)));
       dft8<T, 1>(v);
     } else if (R0 == 2) {
 #pragma unroll
       for (int i = 0; i < 2; ++i) {
         C<T>* u = v + 4 * i;
-        const C<T> w = conj<T>(__ldg(tw + t + i * L8)), w2 = mul<T>(w, w), w3 = mul<T>(w2, w);
-        u[1] = mul<T>(u[1], w); u[2] = mul<T>(u[2], w2); u[3] = mul<T>(u[3], w3);
+        if constexpr (sizeof(T) == 8) {
+          const C<T>* pw = tw + t + i * L8;
+          u[1] = mul<T>(u[1], conj<T>(__ldg(pw))); u[2] = mul<T>(u[2], conj<T>(__ldg(pw + (L >> 2))));
+          u[3] = mul<T>(u[3], conj<T>(__ldg(pw + 2 * (L >> 2))));
+        } else {
+          const C<T> w = conj<T>(__ldg(tw + t + i * L8)), w2 = mul<T>(w, w), w3 = mul<T>(w2, w);
+          u[1] = mul<T>(u[1], w); u[2] = mul<T>(u[2], w2); u[3] = mul<T>(u[3], w3);
+        }
         dft4<T, 1>(u[0], u[1], u[2], u[3]);
       }
     } else {
@@ -118,7 +137,10 @@ struct FftC {
 #pragma unroll
     for (int r = 0; r < 8; ++r) v[r] = buf[sb ^ sw(r << ls)];
     dft8<T, -1>(v);
-    if (ls > 0) twiddle8<T>(v, __ldg(tw + tw_off8(LOGL, R0, ls) + o));
+    if (ls > 0) {
+      if constexpr (sizeof(T) == 8) twiddle8_pow<T, false>(v, tw + pow_off(ls) + o, 1 << ls);
+      else twiddle8<T>(v, __ldg(tw + tw_off8(LOGL, R0, ls) + o));
+    }
 #pragma unroll
     for (int q = 0; q < 8; ++q) buf[sb ^ sw(q << ls)] = v[q];
   }
@@ -128,7 +150,10 @@ struct FftC {
     C<T> v[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) v[r] = buf[sb ^ sw(r << ls)];
-    if (ls > 0) twiddle8<T>(v, conj<T>(__ldg(tw + tw_off8(LOGL, R0, ls) + o)));
+    if (ls > 0) {
+      if constexpr (sizeof(T) == 8) twiddle8_pow<T, true>(v, tw + pow_off(ls) + o, 1 << ls);
+      else twiddle8<T>(v, conj<T>(__ldg(tw + tw_off8(LOGL, R0, ls) + o)));
+    }
     dft8<T, 1>(v);
 #pragma unroll
     for (int q = 0; q < 8; ++q) buf[sb ^ sw(q << ls)] = v[q];

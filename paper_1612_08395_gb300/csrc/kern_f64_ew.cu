@@ -37,24 +37,31 @@ void launch_to_f32(const double* src, float* dst, size_t n, cudaStream_t s) {
   k_to_f32<<<ew_grid(n), 256, 0, s>>>(src, dst, n);
 }
 
-// Stage twiddle tables of a length 2^logL transform: stages in DIF order,
-// the table of stage (R, s) holds exp(-2 pi i o/(R s)) for o < s, tables
-// concatenated (the radix-8 offsets are tw_off8).  Computed in FP64.
+// Stage twiddle tables of a length 2^logL transform, stages in DIF order,
+// tables concatenated.  FP32: the table of stage (R, s) holds
+// exp(-2 pi i o/(R s)) for o < s (the radix-8 offsets are tw_off8); the
+// butterflies form the powers they need.  FP64: the table of stage (R, s)
+// holds every power, exp(-2 pi i o q/(R s)) at (q-1) s + o for q = 1..R-1
+// (offsets FftC::pow_off; fewer than 2^logL entries in all).  Computed in FP64.
 __global__ void k_twiddles(double2* t64, float2* t32, int logL) {
   const int r0 = logL % 3;
   const int L = 1 << logL;
-  int off = 0;
+  int off = 0, off64 = 0;
   int R = r0 ? (1 << r0) : 8;
   int s = L / R;
   for (;;) {
     for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < s; o += gridDim.x * blockDim.x) {
       double sn, cs;
       sincospi(-2.0 * (double)o / ((double)R * (double)s), &sn, &cs);
-      t64[off + o] = make_double2(cs, sn);
       t32[off + o] = make_float2((float)cs, (float)sn);
+      for (int q = 1; q < R; ++q) {  // o q < R s: the argument stays in (-2, 0]
+        sincospi(-2.0 * (double)(o * q) / ((double)R * (double)s), &sn, &cs);
+        t64[off64 + (q - 1) * s + o] = make_double2(cs, sn);
+      }
     }
     if (s == 1) break;
     off += s;
+    off64 += (R - 1) * s;
     R = 8;
     s /= 8;
   }
