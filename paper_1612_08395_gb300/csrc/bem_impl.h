@@ -131,7 +131,11 @@ struct PassArgs {
   double* partC;
   Scalars* sc;
   unsigned int* kerr;   // sticky error word (may be null: errors then go unreported)
-  int use_band;         // fixed-set CG loop: restrict the passes to rows sc->band0 .. band1
+  int use_band;         // 1: fixed-set CG loop, the passes work on rows sc->band0 .. band1
+                        // only; 2: the plain transform of the FP64 residual (A_PLAIN,
+                        // B_CONV, C_GAP) works on rows band_lo .. band_hi only
+  int band_lo, band_hi; // use_band = 2: rows holding every nonzero input; the outputs of
+                        // the other rows are left unwritten
   // Tensor map (device memory) of W as (M+1) rows of 2 rows_w reals with boxes
   // of 2 nbA reals x w_box rows: the persistent pass C stages a row group's W
   // columns with 2D TMA loads.  Null: 16-byte cp.async instead.

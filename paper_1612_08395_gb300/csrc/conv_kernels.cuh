@@ -564,6 +564,10 @@ __device__ __forceinline__ void pass_ap_body(const PassArgs<T>& a) {
     g0 = sc->band0 / nb;
     gend = sc->band1 >= sc->band0 ? sc->band1 / nb + 1 : g0;
   }
+  if (MODE == A_PLAIN && a.use_band == 2) {  // a residual whose input lies in rows band_lo .. band_hi
+    g0 = a.band_lo / nb;
+    gend = a.band_hi >= a.band_lo ? min(a.band_hi / nb + 1, G) : g0;
+  }
   int g = g0 + blockIdx.x;
   if (g < gend) pro_prefetch<T, MODE>(a, st, ss, g * nb, min(nb, nrows - g * nb), ncols, nb, &bar);
   for (; g < gend; g += gridDim.x) {
@@ -684,8 +688,8 @@ __device__ __forceinline__ void pass_b_body(const PassArgs<T>& a) {
   // rows of W that can be nonzero: all, or the contact band in the fixed-set CG loop
   int ylo = 0, yhi = rin - 1;
   if (MODE == B_CONV && a.use_band) {
-    ylo = a.sc->band0;
-    yhi = min(a.sc->band1, rin - 1);
+    ylo = a.use_band == 2 ? a.band_lo : a.sc->band0;
+    yhi = min(a.use_band == 2 ? a.band_hi : a.sc->band1, rin - 1);
   }
 
   Cx v[8];
@@ -913,8 +917,8 @@ __device__ __forceinline__ void pass_b16_body(const PassArgs<T>& a) {
   const size_t coff = (size_t)(act ? kx : 0) * rin;
   int ylo = 0, yhi = rin - 1;
   if (a.use_band) {
-    ylo = a.sc->band0;
-    yhi = min(a.sc->band1, rin - 1);
+    ylo = a.use_band == 2 ? a.band_lo : a.sc->band0;
+    yhi = min(a.use_band == 2 ? a.band_hi : a.sc->band1, rin - 1);
   }
 
   Cx v[16];
@@ -1512,6 +1516,10 @@ __device__ __forceinline__ void pass_cp_body(const PassArgs<T>& a) {
   if (MODE == C_CG_R && a.use_band) {
     g0 = sc->band0 / nb;
     gend = sc->band1 >= sc->band0 ? sc->band1 / nb + 1 : g0;
+  }
+  if (MODE == C_GAP && a.use_band == 2) {  // the residual on rows band_lo .. band_hi only
+    g0 = a.band_lo / nb;
+    gend = a.band_hi >= a.band_lo ? min(a.band_hi / nb + 1, G) : g0;
   }
   int g = g0 + blockIdx.x;
   if (g < gend) {

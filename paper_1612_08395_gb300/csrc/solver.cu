@@ -1107,7 +1107,10 @@ int collect(bem_ctx* h, const T* p, const T* g, int use_set, bem_result* r) {
 }
 
 // FP64 gap of the FP64 pressure in io64: g64 = A K p64 + h - d  (into f64.g).
-int gap64(bem_ctx* h, double d) {
+// With rows band_lo <= band_hi holding every nonzero p64, the transform works
+// on those rows only and g64 is formed there only (its other rows keep what
+// they held): the adhesive refinement needs the residual on the held set alone.
+int gap64(bem_ctx* h, double d, int band_lo = 0, int band_hi = -1) {
   CKR(ensure_fields<double>(h));
   PrecFields<double>& f = h->f64;
   const size_t n = (size_t)h->nx * h->ny;
@@ -1115,6 +1118,11 @@ int gap64(bem_ctx* h, double d) {
   PassArgs<double> a = make_args<double>(h);
   a.f.src = h->io64;
   a.sc = nullptr;
+  if (band_hi >= band_lo && band_lo >= 0 && band_hi < h->ny) {
+    a.use_band = 2;
+    a.band_lo = band_lo;
+    a.band_hi = band_hi;
+  }
   launch_pass_a<double>(a, A_PLAIN, h->stream);
   launch_pass_b<double>(a, B_CONV, h->stream);
   launch_pass_c<double>(a, C_GAP, h->stream);
@@ -1135,11 +1143,15 @@ int max_abs_on_set(bem_ctx* h, const double* x, double* out) {
 // (one FP64 convolution), chooses the set S, solves A K dp + g64 = 0 on S with
 // the FP32 fixed-set CG, and adds dp.  Non-adhesive: S = {p > 0} U {g < 0} and
 // p is projected onto p >= 0 after the update; adhesive: S is held and tension
-// is allowed.  Stops when max_S |g64| <= tol64 * max_S |h - d|.
-int refine_here(bem_ctx* h, double d, bool adhesive, int sweeps, double tol64, double tol32, StepOut* so) {
+// is allowed.  Stops when max_S |g64| <= tol64 * max_S |h - d|.  Adhesive:
+// rows band_lo .. band_hi hold S (when band_lo <= band_hi), and the FP64 gap
+// is formed on them only.
+int refine_here(bem_ctx* h, double d, bool adhesive, int sweeps, double tol64, double tol32, StepOut* so,
+                int band_lo = 0, int band_hi = -1) {
   const size_t n = (size_t)h->nx * h->ny;
   for (int s = 0; s < sweeps; ++s) {
-    CKR(gap64(h, d));
+    if (adhesive) CKR(gap64(h, d, band_lo, band_hi));
+    else CKR(gap64(h, d));
     if (!adhesive) { launch_active_set(h->io64, h->f64.g, h->S, n, h->stream); h->launches += 1; }
     double res = 0, scale = 0;
     CKR(max_abs_on_set(h, h->f64.g, &res));
@@ -1173,6 +1185,8 @@ int refine(bem_ctx* h, double d, bool adhesive, int sweeps, double tol64, double
     else launch_box_overlap(h->plan64, h->h64, d, h->sc, h->stream);
     h->launches += 1;
     CKR(read_scalars(h));
+    // rows of the held set (adhesive): its box, in this grid and at the sub-grid's origin
+    const int b0 = h->sc_host->band0, b1 = h->sc_host->band1;
     bem_ctx* sub = nullptr;
     CKR(pick_sub(h, &sub));
     if (sub) {
@@ -1183,12 +1197,13 @@ int refine(bem_ctx* h, double d, bool adhesive, int sweeps, double tol64, double
                                 sub->nx, sub->ny, h->stream);
       launch_box_copy64(h->h64, h->nx, h->ny, x0, y0, sub->h64, sub->nx, sub->ny, 1.0e6, h->stream);
       sub->timing = h->timing;
-      CKR(refine_here(sub, d, adhesive, sweeps, tol64, tol32, so));
+      CKR(refine_here(sub, d, adhesive, sweeps, tol64, tol32, so, 0, b1 - b0));
       launch_box_scatter<double>(sub->io64, h->io64, h->nx, h->ny, x0, y0, sub->nx, sub->ny, h->stream);
       h->launches += 3;
       absorb_sub(h, sub);
       return BEM_OK;
     }
+    return refine_here(h, d, adhesive, sweeps, tol64, tol32, so, b0, b1);
   }
   return refine_here(h, d, adhesive, sweeps, tol64, tol32, so);
 }
